@@ -1,0 +1,244 @@
+/*
+ * hbmc.h - C ABI of the GB300 HBMC-ICCG solver (libhbmc.so).
+ *
+ * Solves A x = b for a sparse symmetric positive definite A by IC(0)-
+ * preconditioned CG whose forward and backward substitutions run under
+ * hierarchical block multi-color (HBMC) ordering (Iwashita, Li, Fukaya,
+ * arXiv:1908.00741).  Problem statement: Section 2, Eq. "org"; IC(0)-CG with
+ * A symmetric positive (semi-)definite.
+ *
+ * Conventions for every entry point
+ *   - Input matrices are host CSR: row_ptr int64[n+1] (row_ptr[0] = 0),
+ *     col int32[nnz] strictly ascending inside each row, val double[nnz];
+ *     both triangles stored, numerically symmetric (a_ij == a_ji exactly),
+ *     positive diagonal present in every row.  The library copies them;
+ *     the caller keeps ownership.
+ *   - Vectors passed as *_dev are caller-owned CUDA device pointers of
+ *     doubles on the context's device.  "Original ordering" vectors have
+ *     length n; "reordered" vectors (the *_bar step functions) have length
+ *     n_pad in HBMC order.
+ *   - All GPU work is enqueued on the context's stream (hbmc_set_stream;
+ *     default: the legacy default stream).  Functions that return numeric
+ *     results synchronize that stream before returning; hbmc_precond and the
+ *     step functions are asynchronous.
+ *   - Errors are reported only through the returned status; no exception,
+ *     abort or device trap crosses the ABI.  hbmc_last_error() gives a
+ *     one-line description of the most recent failure on a context.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef HBMC_H_
+#define HBMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hbmc_status {
+  HBMC_OK = 0,
+  HBMC_ERR_INVALID_ARG = 1,   /* bad sizes, pointers, CSR or options */
+  HBMC_ERR_NOT_SPD_PIVOT = 2, /* IC(0) met a pivot that is not positive and finite */
+  HBMC_ERR_BREAKDOWN = 3,     /* CG: p.q or r.z not positive and finite */
+  HBMC_NOT_CONVERGED = 4,     /* maxit reached before the tolerance */
+  HBMC_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+  HBMC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  HBMC_ERR_OOM = 7,           /* device or host allocation failed */
+  HBMC_ERR_NOT_FACTORED = 8,  /* solve requested before a successful hbmc_ic0 */
+  HBMC_ERR_NO_DEVICE = 9      /* context built with host_only, or no CUDA device */
+} hbmc_status;
+
+/* Blocking rule for the BMC blocks (Section 4.1). */
+enum {
+  HBMC_BLOCK_ALGEBRAIC = 0, /* Section 5.1: seed = minimal-numbered unassigned unknown,
+                               grown by the minimal-numbered unassigned neighbour */
+  HBMC_BLOCK_BOXES = 1      /* geometric bx*by*bz boxes of a lexicographic grid (x fastest) */
+};
+
+/* Arithmetic of the preconditioner substitutions.  The CG recurrences, dot
+ * products, SpMV and the IC(0) factorization are always FP64. */
+enum { HBMC_PREC_F64 = 0, HBMC_PREC_F32 = 1 };
+
+/* How the CG loop is driven on the device. */
+enum {
+  HBMC_LOOP_GRAPH = 0, /* one CUDA graph launch per solve; a device-side while node
+                          runs the iterations, convergence decided on the GPU */
+  HBMC_LOOP_HOST = 1   /* host launches iterations and polls a device flag */
+};
+
+typedef struct hbmc_options {
+  int32_t blocking;  /* HBMC_BLOCK_ALGEBRAIC (default) or HBMC_BLOCK_BOXES */
+  int64_t grid[3];   /* nx, ny, nz for HBMC_BLOCK_BOXES (n must equal nx*ny*nz) */
+  int32_t box[3];    /* bx, by, bz for HBMC_BLOCK_BOXES (bx*by*bz must equal bs) */
+  int32_t precision; /* HBMC_PREC_F64 (default) or HBMC_PREC_F32 */
+  int32_t loop_mode; /* HBMC_LOOP_GRAPH (default) or HBMC_LOOP_HOST */
+  int32_t host_only; /* nonzero: compute the ordering and layouts on the host only,
+                        touch no GPU (inspection and CPU tests) */
+  int32_t device;    /* CUDA device ordinal; -1 = the current device */
+  int32_t check_every; /* HBMC_LOOP_HOST: iterations between flag polls (default 16) */
+} hbmc_options;
+
+/* Fills *opt with the defaults. */
+void hbmc_default_options(hbmc_options *opt);
+
+typedef struct hbmc_ctx hbmc_ctx; /* opaque; owns every buffer it allocates */
+
+typedef struct hbmc_info_t {
+  int64_t n;          /* unknowns */
+  int64_t n_pad;      /* unknowns plus dummies (Section 4.2.1) */
+  int64_t nnz;        /* nonzeros of A */
+  int64_t nnz_lower;  /* strict lower nonzeros of A = nonzeros of L off the diagonal */
+  int32_t bs, w;      /* block size b_s and level-1 width w */
+  int32_t nc;         /* colors n_c */
+  int64_t nblocks;    /* BMC blocks (before padding) */
+  int64_t ntiles;     /* level-1 blocks of all colors (after padding) */
+  int64_t sell_entries_a;   /* stored SpMV entries including slice padding */
+  int64_t sell_entries_l;   /* stored forward-sweep entries including padding */
+  int64_t sell_entries_u;   /* stored backward-sweep entries including padding */
+  int32_t precision;
+  int32_t factored;   /* 1 after a successful hbmc_ic0 */
+  size_t device_bytes;      /* device memory held by the context */
+} hbmc_info_t;
+
+/*
+ * hbmc_build - block, color and reorder A, then lay it out on the device.
+ *
+ * Section 4.1 (BMC: blocks of bs unknowns, greedy block coloring; the
+ * blocking heuristic and greedy coloring of Section 5.1), Section 4.2
+ * (level-1 blocks of w consecutive same-color BMC blocks, Eq. "simd-block";
+ * secondary reordering; dummy unknowns so every color is a multiple of bs*w),
+ * Section 4.3.2 (SELL storage with slice size w).
+ *
+ * n, row_ptr, col, val: host CSR of A (see conventions).  n == 0 gives a
+ * valid empty context.  bs in [1, 64]; w in {1, 2, 4, 8, 16, 32}.
+ * opt may be NULL (defaults).  On success *out receives a new context that
+ * the caller frees with hbmc_destroy; on failure *out is NULL.
+ * Errors: INVALID_ARG (CSR not sorted, not symmetric, missing or
+ * non-positive diagonal, bad bs/w/options), OOM, CUDA, NO_DEVICE.
+ */
+hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                       int32_t bs, int32_t w, const hbmc_options *opt, hbmc_ctx **out);
+
+/* Releases every resource of ctx (NULL is ignored). */
+void hbmc_destroy(hbmc_ctx *ctx);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * hbmc_build in this thread when ctx is NULL).  Valid until the next call. */
+const char *hbmc_last_error(const hbmc_ctx *ctx);
+
+/* Static name of a status code. */
+const char *hbmc_status_string(hbmc_status s);
+
+hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info);
+
+/*
+ * hbmc_get_ordering - copy the host-side ordering out (works for host_only
+ * contexts).  pi: int64[n], the position of original unknown i in the padded
+ * HBMC numbering (the reordering function pi of Section 3).  color_ptr:
+ * int64[nc+1], color c occupies [color_ptr[c], color_ptr[c+1]).  block_of:
+ * int64[n] BMC block of each unknown; block_color: int32[nblocks].  Any
+ * output pointer may be NULL.
+ */
+hbmc_status hbmc_get_ordering(const hbmc_ctx *ctx, int64_t *pi, int64_t *color_ptr,
+                              int64_t *block_of, int32_t *block_color);
+
+/*
+ * hbmc_get_matrix - host copy of Abar = P A P^T (Section 3, Eq. "AB") on the
+ * padded index space (dummy rows are identity rows): row_ptr int64[n_pad+1],
+ * col int32[nnz + n_pad - n], val double[nnz + n_pad - n], sorted columns.
+ */
+hbmc_status hbmc_get_matrix(const hbmc_ctx *ctx, int64_t *row_ptr, int32_t *col, double *val);
+
+/* Bind the context to a CUDA stream (a cudaStream_t, e.g. from
+ * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */
+hbmc_status hbmc_set_stream(hbmc_ctx *ctx, void *stream);
+
+/* Switch the substitution arithmetic (HBMC_PREC_F64 or HBMC_PREC_F32).  The
+ * FP32 factor is a rounded copy of the FP64 factor made by hbmc_ic0. */
+hbmc_status hbmc_set_precision(hbmc_ctx *ctx, int32_t precision);
+
+/*
+ * hbmc_ic0 - shifted IC(0) factorization of Abar on the GPU.
+ *
+ * Section 2, Eq. "ILU" (A ~= L U with L, U on the patterns of the lower and
+ * upper triangles of A; for IC(0) U = L^T), with the diagonal shift of the
+ * shifted ICCG of Section 5.1: the factored matrix has diagonal
+ * (1 + shift) * a_ii and unchanged off-diagonals.  Runs color by color with
+ * the same level-1 / lane structure as the substitutions.  shift > -1.
+ * bad_row (may be NULL) receives -1 on success, or on HBMC_ERR_NOT_SPD_PIVOT
+ * the original index of the first row (in HBMC order) whose pivot was not
+ * positive and finite.  Synchronizes the stream.
+ */
+hbmc_status hbmc_ic0(hbmc_ctx *ctx, double shift, int64_t *bad_row);
+
+/*
+ * hbmc_get_factor - host copy of the FP64 factor: lower holds l_ij at the
+ * position of each entry of Abar (hbmc_get_matrix layout; 0 for diagonal and
+ * upper entries), diag holds l_ii (n_pad).  Either pointer may be NULL.
+ */
+hbmc_status hbmc_get_factor(const hbmc_ctx *ctx, double *lower, double *diag);
+
+/*
+ * hbmc_precond - z = (L L^T)^{-1} r in the original ordering: permute in,
+ * forward substitution y = L^{-1} r (Eq. "for") over colors 1..n_c,
+ * backward substitution z = L^{-T} y (Eq. "back") over colors n_c..1,
+ * permute out.  r_dev, z_dev: device double[n] (may not alias).
+ * Asynchronous.  Errors: NOT_FACTORED, INVALID_ARG, CUDA.
+ */
+hbmc_status hbmc_precond(hbmc_ctx *ctx, const double *r_dev, double *z_dev);
+
+/*
+ * hbmc_iccg - solve A x = b by IC(0)-preconditioned CG (Section 2; stopping
+ * rule of Section 5.1: 2-norm relative residual ||r_k|| / ||b|| < tol, with
+ * the recurrence residual).
+ *
+ * b_dev: device double[n], original ordering.  x_dev: device double[n]; on
+ * entry the initial guess, on exit the solution.  tol > 0; maxit >= 0.
+ * iters: CG iterations performed (x updates); relres: final recurrence
+ * relative residual; true_relres: ||b - A x|| / ||b|| recomputed in FP64
+ * after the loop.  Any output pointer may be NULL.  Synchronizes the stream.
+ * Returns OK, NOT_CONVERGED (maxit reached; x holds the last iterate),
+ * BREAKDOWN, NOT_FACTORED, INVALID_ARG or CUDA.
+ */
+hbmc_status hbmc_iccg(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double tol, int64_t maxit,
+                      int64_t *iters, double *relres, double *true_relres);
+
+/*
+ * hbmc_iccg_host - hbmc_iccg with HOST vectors b_host[n] and x_host[n]
+ * (x_host is the initial guess on entry).  Copies b and x0 to the device,
+ * solves and copies x back, all on the context's stream.  Page-locked host
+ * memory gives the fastest copies.
+ */
+hbmc_status hbmc_iccg_host(hbmc_ctx *ctx, const double *b_host, double *x_host, double tol,
+                           int64_t maxit, int64_t *iters, double *relres, double *true_relres);
+
+/*
+ * hbmc_residual_history - copy the recurrence relative residuals of the last
+ * hbmc_iccg call: hist[0] for the initial guess, hist[k] after iteration k,
+ * for k = 0..min(iters, cap-1).  Returns the number written in *count.
+ * Recording costs one store per iteration and is always on (up to the
+ * capacity fixed at build time, 100000 entries).
+ */
+hbmc_status hbmc_residual_history(const hbmc_ctx *ctx, double *hist, int64_t cap, int64_t *count);
+
+/*
+ * Step functions on reordered, padded vectors (length n_pad, HBMC order),
+ * for testing and for callers that keep their vectors in HBMC order.
+ * They run the kernels of the solve one at a time and are asynchronous.
+ *
+ * hbmc_fwd_bar: y = L^{-1} r (Eq. "for"; colors 1..n_c, Eqs. "for2",
+ *   "for3"; inside a level-1 block the bs steps of Eqs. "y2-2", "y2-3").
+ * hbmc_bwd_bar: z = L^{-T} y (Eq. "back"; colors n_c..1).
+ * hbmc_spmv_bar: q = Abar p.
+ * In HBMC_PREC_F32 mode the substitutions compute in FP32 and the results
+ * are widened to double on output.
+ */
+hbmc_status hbmc_fwd_bar(hbmc_ctx *ctx, const double *r_dev, double *y_dev);
+hbmc_status hbmc_bwd_bar(hbmc_ctx *ctx, const double *y_dev, double *z_dev);
+hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HBMC_H_ */

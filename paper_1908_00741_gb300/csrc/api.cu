@@ -1,0 +1,599 @@
+// C ABI of libhbmc.so: context lifetime, device layout upload, IC(0), the
+// preconditioner and the CG solve (CUDA graph with a device-side while node,
+// or a host-driven loop).
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hbmc.h"
+#include "hbmc_internal.h"
+#include "kernels.h"
+
+using hbmc::DeviceLayout;
+using hbmc::HostLayout;
+using hbmc::Scalars;
+
+struct hbmc_ctx {
+  HostLayout h;
+  DeviceLayout d;
+  hbmc_options opt{};
+  std::string err;
+  int device = 0;
+  bool host_only = false;
+  bool factored = false;
+  int32_t precision = HBMC_PREC_F64;
+  cudaStream_t stream = nullptr;     // user stream (nullptr = legacy default)
+  cudaStream_t cap[2] = {nullptr, nullptr};  // private streams used for graph capture
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  Scalars *h_sc = nullptr;           // page-locked mirror of the device scalars
+  double *stage_b = nullptr, *stage_x = nullptr;  // device staging for hbmc_iccg_host
+  std::vector<void *> allocs;
+  int64_t last_iters = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+hbmc_status set_err(hbmc_ctx *c, hbmc_status s, const std::string &msg) {
+  if (c) c->err = msg; else g_err = msg;
+  return s;
+}
+
+hbmc_status cuda_err(hbmc_ctx *c, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return set_err(c, e == cudaErrorMemoryAllocation ? HBMC_ERR_OOM : HBMC_ERR_CUDA, m);
+}
+
+#define CK(call)                                               \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call);    \
+  } while (0)
+
+template <class T>
+hbmc_status dalloc(hbmc_ctx *ctx, T *&p, size_t count) {
+  p = nullptr;
+  size_t bytes = (count ? count : 1) * sizeof(T);
+  void *q = nullptr;
+  CK(cudaMalloc(&q, bytes));
+  ctx->allocs.push_back(q);
+  ctx->d.bytes += bytes;
+  CK(cudaMemset(q, 0, bytes));
+  p = static_cast<T *>(q);
+  return HBMC_OK;
+}
+
+template <class T>
+hbmc_status dupload(hbmc_ctx *ctx, T *&p, const std::vector<T> &v) {
+  hbmc_status s = dalloc(ctx, p, v.size());
+  if (s != HBMC_OK) return s;
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HBMC_OK;
+}
+
+#define TRY(expr)                          \
+  do {                                     \
+    hbmc_status s_ = (expr);               \
+    if (s_ != HBMC_OK) return s_;          \
+  } while (0)
+
+hbmc_status upload(hbmc_ctx *ctx) {
+  const HostLayout &h = ctx->h;
+  DeviceLayout &d = ctx->d;
+  d.n = h.n;
+  d.n_pad = h.n_pad;
+  d.nnz_lower = h.nnz_lower;
+  d.bs = h.bs;
+  d.w = h.w;
+  d.nc = h.nc;
+  d.tile_ptr = h.tile_ptr;
+  std::vector<int32_t> pi32(h.pi.begin(), h.pi.end());
+  TRY(dupload(ctx, d.inv, h.inv));
+  TRY(dupload(ctx, d.pi, pi32));
+  TRY(dupload(ctx, d.a_ptr, h.a_ptr));
+  TRY(dupload(ctx, d.a_col, h.a_col));
+  TRY(dupload(ctx, d.a_val, h.a_val));
+  TRY(dupload(ctx, d.fo_ptr, h.fo_ptr));
+  TRY(dupload(ctx, d.fi_ptr, h.fi_ptr));
+  TRY(dupload(ctx, d.bo_ptr, h.bo_ptr));
+  TRY(dupload(ctx, d.bi_ptr, h.bi_ptr));
+  TRY(dupload(ctx, d.fo_col, h.fo_col));
+  TRY(dupload(ctx, d.bo_col, h.bo_col));
+  TRY(dupload(ctx, d.fi_m, h.fi_m));
+  TRY(dupload(ctx, d.bi_m, h.bi_m));
+  TRY(dalloc(ctx, d.fo_val, h.fo_col.size()));
+  TRY(dalloc(ctx, d.bo_val, h.bo_col.size()));
+  TRY(dalloc(ctx, d.fi_val, h.fi_m.size()));
+  TRY(dalloc(ctx, d.bi_val, h.bi_m.size()));
+  TRY(dalloc(ctx, d.fo_val32, h.fo_col.size()));
+  TRY(dalloc(ctx, d.bo_val32, h.bo_col.size()));
+  TRY(dalloc(ctx, d.fi_val32, h.fi_m.size()));
+  TRY(dalloc(ctx, d.bi_val32, h.bi_m.size()));
+  TRY(dalloc(ctx, d.dinv, h.n_pad));
+  TRY(dalloc(ctx, d.dinv32, h.n_pad));
+  TRY(dupload(ctx, d.lrp, h.lrp));
+  TRY(dupload(ctx, d.lci, h.lci));
+  TRY(dupload(ctx, d.laval, h.laval));
+  TRY(dupload(ctx, d.adiag, h.adiag));
+  TRY(dalloc(ctx, d.lval, h.nnz_lower));
+  TRY(dalloc(ctx, d.ldiag, h.n_pad));
+  TRY(dupload(ctx, d.lmap_f, h.lmap_f));
+  TRY(dupload(ctx, d.lmap_b, h.lmap_b));
+  const size_t nv = (size_t)(h.n_pad + hbmc::kGuard);
+  TRY(dalloc(ctx, d.b, nv));
+  TRY(dalloc(ctx, d.x, nv));
+  TRY(dalloc(ctx, d.r, nv));
+  TRY(dalloc(ctx, d.z, nv));
+  TRY(dalloc(ctx, d.p, nv));
+  TRY(dalloc(ctx, d.q, nv));
+  TRY(dalloc(ctx, d.y, nv));
+  TRY(dalloc(ctx, d.t, nv));
+  TRY(dalloc(ctx, d.y32, nv));
+  d.part_len = hbmc::partials_needed(d);
+  TRY(dalloc(ctx, d.part, (size_t)d.part_len));
+  TRY(dalloc(ctx, d.hist, (size_t)hbmc::kHistCap));
+  TRY(dalloc(ctx, d.sc, 1));
+  TRY(dalloc(ctx, ctx->stage_b, (size_t)h.n));
+  TRY(dalloc(ctx, ctx->stage_x, (size_t)h.n));
+  CK(cudaMallocHost(&ctx->h_sc, sizeof(Scalars)));
+  std::memset(ctx->h_sc, 0, sizeof(Scalars));
+  CK(cudaStreamCreateWithFlags(&ctx->cap[0], cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&ctx->cap[1], cudaStreamNonBlocking));
+  CK(cudaDeviceSynchronize());
+  return HBMC_OK;
+}
+
+hbmc_status need_device(hbmc_ctx *ctx) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  if (ctx->host_only) return set_err(ctx, HBMC_ERR_NO_DEVICE, "context was built with host_only");
+  return HBMC_OK;
+}
+
+// Capture the whole solve as one graph: init, a while node running one CG
+// iteration per pass (its condition is cleared on the device when the solve
+// is done), then the permutation out and the true residual.
+hbmc_status build_graph(hbmc_ctx *ctx, int prec) {
+  const DeviceLayout &d = ctx->d;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  ctx->graph[prec] = g;
+  cudaGraphConditionalHandle handle;
+  CK(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
+  cudaStream_t s = ctx->cap[0], s2 = ctx->cap[1];
+  CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  hbmc::enqueue_init(d, prec, s);
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) {
+    cudaGraph_t junk;
+    cudaStreamEndCapture(s, &junk);
+    return cuda_err(ctx, e, "cudaStreamGetCaptureInfo");
+  }
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  e = cudaGraphAddNode(&loop, g, dv.data(), nullptr, dv.size(), &cp);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) {
+    cudaGraph_t junk;
+    cudaStreamEndCapture(s, &junk);
+    return cuda_err(ctx, e, "adding the CG while node");
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    hbmc::enqueue_body(d, prec, s2, true, handle);
+    e = cudaStreamEndCapture(s2, &body);
+  }
+  if (e != cudaSuccess) {
+    cudaGraph_t junk;
+    cudaStreamEndCapture(s, &junk);
+    return cuda_err(ctx, e, "capturing the CG iteration");
+  }
+  hbmc::enqueue_final(d, s);
+  CK(cudaStreamEndCapture(s, &g));
+  CK(cudaGetLastError());
+  CK(cudaGraphInstantiate(&ctx->exec[prec], g, 0));
+  return HBMC_OK;
+}
+
+hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double tol, int64_t maxit,
+                      int64_t *iters, double *relres, double *true_relres) {
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  if (true_relres) *true_relres = 0.0;
+  if (!(tol > 0.0) || maxit < 0) return set_err(ctx, HBMC_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 0");
+  if (ctx->h.n == 0) {
+    ctx->last_iters = 0;
+    return HBMC_OK;
+  }
+  if (!b_dev || !x_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "hbmc_ic0 has not succeeded on this context");
+  const int prec = ctx->precision;
+  const DeviceLayout &d = ctx->d;
+  Scalars init;
+  std::memset(&init, 0, sizeof init);
+  init.tol = tol;
+  init.maxit = maxit;
+  init.bad_row = LLONG_MAX;
+  init.user_b = b_dev;
+  init.user_x = x_dev;
+  *ctx->h_sc = init;
+  CK(cudaMemcpyAsync(d.sc, ctx->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->opt.loop_mode == HBMC_LOOP_GRAPH) {
+    if (!ctx->exec[prec]) TRY(build_graph(ctx, prec));
+    CK(cudaGraphLaunch(ctx->exec[prec], ctx->stream));
+  } else {
+    hbmc::enqueue_init(d, prec, ctx->stream);
+    const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+    for (int64_t k = 0;; k += every) {
+      for (int t = 0; t < every; ++t) hbmc::enqueue_body(d, prec, ctx->stream, false, 0);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(ctx->h_sc, d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (ctx->h_sc->done) break;
+    }
+    hbmc::enqueue_final(d, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_sc, d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const Scalars &r = *ctx->h_sc;
+  ctx->last_iters = r.iters;
+  if (iters) *iters = r.iters;
+  if (relres) *relres = r.relres;
+  if (true_relres) *true_relres = r.true_relres;
+  switch (r.status) {
+    case hbmc::ST_CONVERGED: return HBMC_OK;
+    case hbmc::ST_MAXIT: return set_err(ctx, HBMC_NOT_CONVERGED, "maxit reached before the tolerance");
+    case hbmc::ST_BREAKDOWN: return set_err(ctx, HBMC_ERR_BREAKDOWN, "CG breakdown: p.q or r.z not positive and finite");
+    default: return set_err(ctx, HBMC_ERR_CUDA, "solve ended without a final status");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void hbmc_default_options(hbmc_options *opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->blocking = HBMC_BLOCK_ALGEBRAIC;
+  opt->precision = HBMC_PREC_F64;
+  opt->loop_mode = HBMC_LOOP_GRAPH;
+  opt->device = -1;
+  opt->check_every = 16;
+}
+
+const char *hbmc_status_string(hbmc_status s) {
+  switch (s) {
+    case HBMC_OK: return "HBMC_OK";
+    case HBMC_ERR_INVALID_ARG: return "HBMC_ERR_INVALID_ARG";
+    case HBMC_ERR_NOT_SPD_PIVOT: return "HBMC_ERR_NOT_SPD_PIVOT";
+    case HBMC_ERR_BREAKDOWN: return "HBMC_ERR_BREAKDOWN";
+    case HBMC_NOT_CONVERGED: return "HBMC_NOT_CONVERGED";
+    case HBMC_ERR_TIMEOUT: return "HBMC_ERR_TIMEOUT";
+    case HBMC_ERR_CUDA: return "HBMC_ERR_CUDA";
+    case HBMC_ERR_OOM: return "HBMC_ERR_OOM";
+    case HBMC_ERR_NOT_FACTORED: return "HBMC_ERR_NOT_FACTORED";
+    case HBMC_ERR_NO_DEVICE: return "HBMC_ERR_NO_DEVICE";
+  }
+  return "HBMC_UNKNOWN_STATUS";
+}
+
+const char *hbmc_last_error(const hbmc_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                       int32_t bs, int32_t w, const hbmc_options *opt, hbmc_ctx **out) {
+  if (!out) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  g_err.clear();
+  hbmc_options o;
+  hbmc_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != HBMC_PREC_F64 && o.precision != HBMC_PREC_F32)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
+  if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown loop mode");
+  hbmc_ctx *ctx = nullptr;
+  try {
+    ctx = new hbmc_ctx();
+  } catch (...) {
+    return set_err(nullptr, HBMC_ERR_OOM, "host allocation failed");
+  }
+  ctx->opt = o;
+  ctx->host_only = o.host_only != 0;
+  ctx->precision = o.precision;
+  hbmc_status s;
+  try {
+    s = hbmc::build_host(n, row_ptr, col, val, bs, w, o, ctx->h, ctx->err);
+  } catch (const std::bad_alloc &) {
+    s = HBMC_ERR_OOM;
+    ctx->err = "host allocation failed";
+  }
+  if (s != HBMC_OK) {
+    g_err = ctx->err;
+    delete ctx;
+    return s;
+  }
+  if (!ctx->host_only) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      g_err = "no CUDA device";
+      delete ctx;
+      return HBMC_ERR_NO_DEVICE;
+    }
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    if (dev >= ndev) {
+      g_err = "device ordinal out of range";
+      delete ctx;
+      return HBMC_ERR_INVALID_ARG;
+    }
+    ctx->device = dev;
+    DeviceGuard guard(dev);
+    cudaError_t e = hbmc::setup_kernels();
+    if (e != cudaSuccess) {
+      s = cuda_err(ctx, e, "setup_kernels");
+    } else {
+      s = upload(ctx);
+    }
+    if (s != HBMC_OK) {
+      g_err = ctx->err;
+      hbmc_destroy(ctx);
+      return s;
+    }
+  }
+  *out = ctx;
+  return HBMC_OK;
+}
+
+void hbmc_destroy(hbmc_ctx *ctx) {
+  if (!ctx) return;
+  if (!ctx->host_only) {
+    DeviceGuard guard(ctx->device);
+    cudaDeviceSynchronize();
+    for (int k = 0; k < 2; ++k) {
+      if (ctx->exec[k]) cudaGraphExecDestroy(ctx->exec[k]);
+      if (ctx->graph[k]) cudaGraphDestroy(ctx->graph[k]);
+      if (ctx->cap[k]) cudaStreamDestroy(ctx->cap[k]);
+    }
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+  }
+  delete ctx;
+}
+
+hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info) {
+  if (!ctx || !info) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null argument");
+  const HostLayout &h = ctx->h;
+  std::memset(info, 0, sizeof *info);
+  info->n = h.n;
+  info->n_pad = h.n_pad;
+  info->nnz = h.nnz;
+  info->nnz_lower = h.n ? (h.nnz - h.n) / 2 : 0;
+  info->bs = h.bs;
+  info->w = h.w;
+  info->nc = h.nc;
+  info->nblocks = h.nblocks;
+  info->ntiles = h.ntiles;
+  info->sell_entries_a = (int64_t)h.a_col.size();
+  info->sell_entries_l = (int64_t)(h.fo_col.size() + h.fi_m.size());
+  info->sell_entries_u = (int64_t)(h.bo_col.size() + h.bi_m.size());
+  info->precision = ctx->precision;
+  info->factored = ctx->factored ? 1 : 0;
+  info->device_bytes = ctx->d.bytes;
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_get_ordering(const hbmc_ctx *ctx, int64_t *pi, int64_t *color_ptr, int64_t *block_of,
+                              int32_t *block_color) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  const HostLayout &h = ctx->h;
+  if (pi && h.n) std::memcpy(pi, h.pi.data(), sizeof(int64_t) * h.n);
+  if (color_ptr) std::memcpy(color_ptr, h.color_ptr.data(), sizeof(int64_t) * (h.nc + 1));
+  if (block_of && h.n) std::memcpy(block_of, h.block_of.data(), sizeof(int64_t) * h.n);
+  if (block_color && h.nblocks) std::memcpy(block_color, h.block_color.data(), sizeof(int32_t) * h.nblocks);
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_get_matrix(const hbmc_ctx *ctx, int64_t *row_ptr, int32_t *col, double *val) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  const HostLayout &h = ctx->h;
+  if (row_ptr) std::memcpy(row_ptr, h.rp.data(), sizeof(int64_t) * h.rp.size());
+  if (col && !h.ci.empty()) std::memcpy(col, h.ci.data(), sizeof(int32_t) * h.ci.size());
+  if (val && !h.av.empty()) std::memcpy(val, h.av.data(), sizeof(double) * h.av.size());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_set_stream(hbmc_ctx *ctx, void *stream) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_set_precision(hbmc_ctx *ctx, int32_t precision) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  if (precision != HBMC_PREC_F64 && precision != HBMC_PREC_F32)
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "unknown precision");
+  ctx->precision = precision;
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_ic0(hbmc_ctx *ctx, double shift, int64_t *bad_row) {
+  if (bad_row) *bad_row = -1;
+  TRY(need_device(ctx));
+  if (!(shift > -1.0) || !(shift < 1e300)) return set_err(ctx, HBMC_ERR_INVALID_ARG, "shift must be > -1 and finite");
+  ctx->factored = false;
+  if (ctx->h.n == 0) {
+    ctx->factored = true;
+    return HBMC_OK;
+  }
+  DeviceGuard guard(ctx->device);
+  hbmc::enqueue_ic0(ctx->d, shift, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_sc, ctx->d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const long long bad = ctx->h_sc->bad_row;
+  if (bad != LLONG_MAX) {
+    int64_t orig = (bad >= 0 && bad < ctx->h.n_pad) ? ctx->h.inv[bad] : -1;
+    if (bad_row) *bad_row = orig;
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "IC(0) pivot not positive at row %lld (reordered %lld)",
+                  (long long)orig, (long long)bad);
+    return set_err(ctx, HBMC_ERR_NOT_SPD_PIVOT, buf);
+  }
+  hbmc::enqueue_scatter_factor(ctx->d, true, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->factored = true;
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_get_factor(const hbmc_ctx *ctx_c, double *lower, double *diag) {
+  hbmc_ctx *ctx = const_cast<hbmc_ctx *>(ctx_c);
+  TRY(need_device(ctx));
+  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "no factor");
+  DeviceGuard guard(ctx->device);
+  const HostLayout &h = ctx->h;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (lower) {
+    std::vector<double> lv(h.nnz_lower);
+    if (h.nnz_lower) CK(cudaMemcpy(lv.data(), ctx->d.lval, sizeof(double) * h.nnz_lower, cudaMemcpyDeviceToHost));
+    std::memset(lower, 0, sizeof(double) * h.ci.size());
+    for (int64_t e = 0; e < h.nnz_lower; ++e) lower[h.l_to_abar[e]] = lv[e];
+  }
+  if (diag && h.n_pad) CK(cudaMemcpy(diag, ctx->d.ldiag, sizeof(double) * h.n_pad, cudaMemcpyDeviceToHost));
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_precond(hbmc_ctx *ctx, const double *r_dev, double *z_dev) {
+  TRY(need_device(ctx));
+  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "hbmc_ic0 has not succeeded on this context");
+  if (ctx->h.n == 0) return HBMC_OK;
+  if (!r_dev || !z_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  hbmc::enqueue_gather_in(d, r_dev, d.r, -1, ctx->stream);
+  hbmc::enqueue_fwd(d, ctx->precision, d.r, false, ctx->stream);
+  hbmc::enqueue_bwd(d, ctx->precision, d.r, 0, false, ctx->stream);
+  hbmc::enqueue_gather_out(d, d.z, z_dev, false, ctx->stream);
+  CK(cudaGetLastError());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_iccg(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double tol, int64_t maxit,
+                      int64_t *iters, double *relres, double *true_relres) {
+  TRY(need_device(ctx));
+  DeviceGuard guard(ctx->device);
+  return solve_dev(ctx, b_dev, x_dev, tol, maxit, iters, relres, true_relres);
+}
+
+hbmc_status hbmc_iccg_host(hbmc_ctx *ctx, const double *b_host, double *x_host, double tol,
+                           int64_t maxit, int64_t *iters, double *relres, double *true_relres) {
+  TRY(need_device(ctx));
+  if (ctx->h.n && (!b_host || !x_host)) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  DeviceGuard guard(ctx->device);
+  const size_t bytes = sizeof(double) * (size_t)ctx->h.n;
+  if (bytes) {
+    CK(cudaMemcpyAsync(ctx->stage_b, b_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->stage_x, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  hbmc_status s = solve_dev(ctx, ctx->stage_b, ctx->stage_x, tol, maxit, iters, relres, true_relres);
+  if (bytes && (s == HBMC_OK || s == HBMC_NOT_CONVERGED || s == HBMC_ERR_BREAKDOWN)) {
+    CK(cudaMemcpyAsync(x_host, ctx->stage_x, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return s;
+}
+
+hbmc_status hbmc_residual_history(const hbmc_ctx *ctx_c, double *hist, int64_t cap, int64_t *count) {
+  hbmc_ctx *ctx = const_cast<hbmc_ctx *>(ctx_c);
+  if (count) *count = 0;
+  TRY(need_device(ctx));
+  if (!hist || cap < 0) return set_err(ctx, HBMC_ERR_INVALID_ARG, "bad history buffer");
+  if (ctx->h.n == 0) return HBMC_OK;
+  int64_t m = ctx->last_iters + 1;
+  if (m > hbmc::kHistCap) m = hbmc::kHistCap;
+  if (m > cap) m = cap;
+  DeviceGuard guard(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (m > 0) CK(cudaMemcpy(hist, ctx->d.hist, sizeof(double) * m, cudaMemcpyDeviceToHost));
+  if (count) *count = m;
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_fwd_bar(hbmc_ctx *ctx, const double *r_dev, double *y_dev) {
+  TRY(need_device(ctx));
+  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "no factor");
+  if (ctx->h.n == 0) return HBMC_OK;
+  if (!r_dev || !y_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  const size_t bytes = sizeof(double) * (size_t)d.n_pad;
+  CK(cudaMemcpyAsync(d.r, r_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  hbmc::enqueue_fwd(d, ctx->precision, d.r, false, ctx->stream);
+  if (ctx->precision == HBMC_PREC_F64)
+    CK(cudaMemcpyAsync(y_dev, d.y, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  else
+    hbmc::enqueue_widen(d.y32, y_dev, d.n_pad, ctx->stream);
+  CK(cudaGetLastError());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_bwd_bar(hbmc_ctx *ctx, const double *y_dev, double *z_dev) {
+  TRY(need_device(ctx));
+  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "no factor");
+  if (ctx->h.n == 0) return HBMC_OK;
+  if (!y_dev || !z_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  const size_t bytes = sizeof(double) * (size_t)d.n_pad;
+  if (ctx->precision == HBMC_PREC_F64)
+    CK(cudaMemcpyAsync(d.y, y_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  else
+    hbmc::enqueue_narrow(y_dev, d.y32, d.n_pad, ctx->stream);
+  hbmc::enqueue_bwd(d, ctx->precision, d.r, 0, false, ctx->stream);
+  CK(cudaMemcpyAsync(z_dev, d.z, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaGetLastError());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev) {
+  TRY(need_device(ctx));
+  if (ctx->h.n == 0) return HBMC_OK;
+  if (!p_dev || !q_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  const size_t bytes = sizeof(double) * (size_t)d.n_pad;
+  CK(cudaMemcpyAsync(d.t, p_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  hbmc::enqueue_spmv(d, d.t, d.q, false, ctx->stream);
+  CK(cudaMemcpyAsync(q_dev, d.q, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaGetLastError());
+  return HBMC_OK;
+}
+
+}  // extern "C"

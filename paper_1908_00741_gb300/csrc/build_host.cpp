@@ -1,0 +1,393 @@
+// Host side of hbmc_build: CSR validation, BMC blocking and greedy block
+// coloring (Sections 4.1 and 5.1), the HBMC secondary reordering with dummy
+// padding (Section 4.2), Abar = P A P^T (Section 3, Eq. "AB"), and the packed
+// device layouts (SELL with slice size w, Section 4.3.2).
+#include <algorithm>
+#include <cstdio>
+#include <functional>
+#include <queue>
+#include <utility>
+
+#include "hbmc_internal.h"
+
+namespace hbmc {
+namespace {
+
+bool fail(std::string &err, const char *msg, int64_t a = -1, int64_t b = -1) {
+  char buf[256];
+  if (a >= 0 && b >= 0)
+    std::snprintf(buf, sizeof buf, "%s (row %lld, col %lld)", msg, (long long)a, (long long)b);
+  else if (a >= 0)
+    std::snprintf(buf, sizeof buf, "%s (%lld)", msg, (long long)a);
+  else
+    std::snprintf(buf, sizeof buf, "%s", msg);
+  err = buf;
+  return false;
+}
+
+// CSR checks: shape, sorted unique columns, positive diagonal, exact symmetry.
+bool validate(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, std::string &err) {
+  if (n < 0) return fail(err, "n < 0");
+  if (n == 0) return true;
+  if (!rp || !ci || !v) return fail(err, "null CSR pointer");
+  if (n >= (int64_t(1) << 31) - 4096) return fail(err, "n too large for int32 column indices");
+  if (rp[0] != 0) return fail(err, "row_ptr[0] != 0");
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return fail(err, "row_ptr decreases at row", i);
+  for (int64_t i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t j = ci[e];
+      if (j < 0 || j >= n) return fail(err, "column out of range", i, j);
+      if (e > rp[i] && ci[e - 1] >= j) return fail(err, "columns not strictly ascending", i, j);
+      if (j == i) {
+        diag = true;
+        if (!(v[e] > 0.0) || !(v[e] < 1e308)) return fail(err, "diagonal not positive and finite", i);
+      }
+      if (!(v[e] == v[e]) || v[e] > 1e308 || v[e] < -1e308) return fail(err, "non-finite value", i, j);
+    }
+    if (!diag) return fail(err, "missing diagonal", i);
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t j = ci[e];
+      if (j <= i) continue;
+      const int32_t *lo = ci + rp[j], *hi = ci + rp[j + 1];
+      const int32_t *f = std::lower_bound(lo, hi, (int32_t)i);
+      if (f == hi || *f != i) return fail(err, "pattern not symmetric", i, j);
+      if (v[rp[j] + (f - lo)] != v[e]) return fail(err, "values not symmetric", i, j);
+    }
+  return true;
+}
+
+// Geometric boxes over a lexicographic grid: box ids lexicographic over the
+// box grid (box x index fastest).
+int64_t blocks_boxes(const hbmc_options &o, std::vector<int64_t> &block_of) {
+  const int64_t nx = o.grid[0], ny = o.grid[1], nz = o.grid[2];
+  const int64_t bx = o.box[0], by = o.box[1], bz = o.box[2];
+  const int64_t mx = (nx + bx - 1) / bx, my = (ny + by - 1) / by, mz = (nz + bz - 1) / bz;
+  int64_t i = 0;
+  for (int64_t z = 0; z < nz; ++z) {
+    const int64_t kz = z / bz;
+    for (int64_t y = 0; y < ny; ++y) {
+      const int64_t ky = y / by;
+      for (int64_t x = 0; x < nx; ++x, ++i) block_of[i] = x / bx + mx * (ky + my * kz);
+    }
+  }
+  return mx * my * mz;
+}
+
+// Algebraic blocking of Section 5.1: a new block starts at the minimal-
+// numbered unassigned unknown and grows by the minimal-numbered unassigned
+// unknown adjacent to its members (min-heap of candidates) until it holds bs
+// unknowns or no adjacent unassigned unknown is left.
+int64_t blocks_algebraic(int64_t n, const int64_t *rp, const int32_t *ci, int32_t bs,
+                         std::vector<int64_t> &block_of) {
+  std::fill(block_of.begin(), block_of.end(), -1);
+  std::vector<int64_t> seen(n, -1);  // block in which an unknown became a candidate
+  std::priority_queue<int64_t, std::vector<int64_t>, std::greater<int64_t>> heap;
+  int64_t nb = 0, seed = 0;
+  for (;;) {
+    while (seed < n && block_of[seed] >= 0) ++seed;
+    if (seed == n) break;
+    const int64_t b = nb++;
+    while (!heap.empty()) heap.pop();
+    int64_t next = seed;
+    for (int32_t size = 1;; ++size) {
+      block_of[next] = b;
+      if (size == bs) break;
+      for (int64_t e = rp[next]; e < rp[next + 1]; ++e) {
+        const int64_t j = ci[e];
+        if (block_of[j] < 0 && seen[j] != b) {
+          seen[j] = b;
+          heap.push(j);
+        }
+      }
+      next = -1;
+      while (!heap.empty()) {
+        const int64_t c = heap.top();
+        heap.pop();
+        if (block_of[c] < 0) {
+          next = c;
+          break;
+        }
+      }
+      if (next < 0) break;
+    }
+  }
+  return nb;
+}
+
+// Greedy block coloring (Section 5.1), blocks visited in id order, each
+// taking the smallest color unused by its already colored neighbours.
+int32_t color_blocks(int64_t n, const int64_t *rp, const int32_t *ci, int64_t nb,
+                     const std::vector<int64_t> &block_of, std::vector<int32_t> &color) {
+  std::vector<int64_t> start(nb + 1, 0), members(n);
+  for (int64_t i = 0; i < n; ++i) start[block_of[i] + 1]++;
+  for (int64_t b = 0; b < nb; ++b) start[b + 1] += start[b];
+  {
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n; ++i) members[fill[block_of[i]]++] = i;
+  }
+  color.assign(nb, -1);
+  std::vector<int64_t> taken;  // taken[c] == b: color c is used by a neighbour of b
+  int32_t nc = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    for (int64_t t = start[b]; t < start[b + 1]; ++t) {
+      const int64_t i = members[t];
+      for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+        const int32_t c = color[block_of[ci[e]]];
+        if (c >= 0) {
+          if ((size_t)c >= taken.size()) taken.resize(c + 1, -1);
+          taken[c] = b;
+        }
+      }
+    }
+    int32_t c = 0;
+    while ((size_t)c < taken.size() && taken[c] == b) ++c;
+    color[b] = c;
+    nc = std::max(nc, c + 1);
+  }
+  return nc;
+}
+
+}  // namespace
+
+hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                       int32_t bs, int32_t w, const hbmc_options &opt, HostLayout &h,
+                       std::string &err) {
+  if (bs < 1 || bs > kMaxBs) {
+    fail(err, "bs must be in [1, 64]", bs);
+    return HBMC_ERR_INVALID_ARG;
+  }
+  if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32)) {
+    fail(err, "w must be 1, 2, 4, 8, 16 or 32", w);
+    return HBMC_ERR_INVALID_ARG;
+  }
+  if (!validate(n, rp, ci, v, err)) return HBMC_ERR_INVALID_ARG;
+  if (opt.blocking == HBMC_BLOCK_BOXES) {
+    if (opt.grid[0] < 1 || opt.grid[1] < 1 || opt.grid[2] < 1 ||
+        opt.grid[0] * opt.grid[1] * opt.grid[2] != n) {
+      fail(err, "box blocking: grid nx*ny*nz must equal n");
+      return HBMC_ERR_INVALID_ARG;
+    }
+    if (opt.box[0] < 1 || opt.box[1] < 1 || opt.box[2] < 1 ||
+        (int64_t)opt.box[0] * opt.box[1] * opt.box[2] != bs) {
+      fail(err, "box blocking: bx*by*bz must equal bs");
+      return HBMC_ERR_INVALID_ARG;
+    }
+  } else if (opt.blocking != HBMC_BLOCK_ALGEBRAIC) {
+    fail(err, "unknown blocking rule", opt.blocking);
+    return HBMC_ERR_INVALID_ARG;
+  }
+
+  h = HostLayout();
+  h.n = n;
+  h.bs = bs;
+  h.w = w;
+  h.nnz = n ? rp[n] : 0;
+
+  // ---- blocking and coloring ------------------------------------------------
+  h.block_of.assign(n, 0);
+  h.nblocks = n == 0 ? 0
+              : opt.blocking == HBMC_BLOCK_BOXES ? blocks_boxes(opt, h.block_of)
+                                                 : blocks_algebraic(n, rp, ci, bs, h.block_of);
+  h.nc = n ? color_blocks(n, rp, ci, h.nblocks, h.block_of, h.block_color) : 0;
+
+  // ---- BMC order, padding and HBMC secondary reordering ---------------------
+  // Block p-th in its color (ascending id) lands in level-1 block p / w at
+  // lane p % w; its l-th member (ascending unknown number) goes to step l.
+  std::vector<int64_t> cnt(h.nc, 0), pos(h.nblocks);
+  for (int64_t b = 0; b < h.nblocks; ++b) pos[b] = cnt[h.block_color[b]]++;
+  h.color_ptr.assign(h.nc + 1, 0);
+  h.tile_ptr.assign(h.nc + 1, 0);
+  for (int32_t c = 0; c < h.nc; ++c) {
+    const int64_t tiles = (cnt[c] + w - 1) / w;
+    h.tile_ptr[c + 1] = h.tile_ptr[c] + tiles;
+    h.color_ptr[c + 1] = h.tile_ptr[c + 1] * bs * w;
+  }
+  h.ntiles = h.tile_ptr[h.nc];
+  h.n_pad = h.color_ptr[h.nc];
+  if (h.n_pad + kGuard >= (int64_t(1) << 31)) {
+    fail(err, "padded size too large for int32 column indices", h.n_pad);
+    return HBMC_ERR_INVALID_ARG;
+  }
+  h.pi.assign(n, 0);
+  h.inv.assign(h.n_pad, -1);
+  {
+    std::vector<int32_t> member(h.nblocks, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t b = h.block_of[i];
+      const int64_t p = pos[b], l = member[b]++;
+      const int64_t k = h.color_ptr[h.block_color[b]] + (p / w) * bs * w + l * w + (p % w);
+      h.pi[i] = k;
+      h.inv[k] = (int32_t)i;
+    }
+  }
+
+  // ---- Abar = P A P^T with identity dummy rows --------------------------------
+  const int64_t np = h.n_pad;
+  h.rp.assign(np + 1, 0);
+  for (int64_t k = 0; k < np; ++k) {
+    const int64_t i = h.inv[k];
+    h.rp[k + 1] = h.rp[k] + (i < 0 ? 1 : rp[i + 1] - rp[i]);
+  }
+  h.ci.resize(h.rp[np]);
+  h.av.resize(h.rp[np]);
+  {
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t k = 0; k < np; ++k) {
+      const int64_t i = h.inv[k], o = h.rp[k];
+      if (i < 0) {
+        h.ci[o] = (int32_t)k;
+        h.av[o] = 1.0;
+        continue;
+      }
+      row.clear();
+      for (int64_t e = rp[i]; e < rp[i + 1]; ++e) row.emplace_back((int32_t)h.pi[ci[e]], v[e]);
+      std::sort(row.begin(), row.end(),
+                [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+                  return a.first < b.first;
+                });
+      for (size_t t = 0; t < row.size(); ++t) {
+        h.ci[o + t] = row[t].first;
+        h.av[o + t] = row[t].second;
+      }
+    }
+  }
+
+  // ---- strict lower CSR (IC(0) input) ----------------------------------------
+  h.lrp.assign(np + 1, 0);
+  h.adiag.assign(np, 0.0);
+  for (int64_t k = 0; k < np; ++k) {
+    int64_t c = 0;
+    for (int64_t e = h.rp[k]; e < h.rp[k + 1]; ++e) {
+      if (h.ci[e] < k) ++c;
+      if (h.ci[e] == k) h.adiag[k] = h.av[e];
+    }
+    h.lrp[k + 1] = h.lrp[k] + c;
+  }
+  h.nnz_lower = h.lrp[np];
+  h.lci.resize(h.nnz_lower);
+  h.laval.resize(h.nnz_lower);
+  h.l_to_abar.resize(h.nnz_lower);
+  for (int64_t k = 0; k < np; ++k) {
+    int64_t o = h.lrp[k];
+    for (int64_t e = h.rp[k]; e < h.rp[k + 1] && h.ci[e] < k; ++e, ++o) {
+      h.lci[o] = h.ci[e];
+      h.laval[o] = h.av[e];
+      h.l_to_abar[o] = e;
+    }
+  }
+
+  // ---- SELL layouts, one slice per (level-1 block, step) ----------------------
+  const int64_t nslices = np / w;
+  const int64_t guard = np;  // padded slots gather index n_pad (always 0)
+  const int64_t tile_rows = (int64_t)bs * w;
+
+  // SpMV: all entries of each row, ascending columns.
+  h.a_ptr.assign(nslices + 1, 0);
+  for (int64_t s = 0; s < nslices; ++s) {
+    int64_t len = 0;
+    for (int32_t j = 0; j < w; ++j) {
+      const int64_t k = s * w + j;
+      len = std::max(len, h.rp[k + 1] - h.rp[k]);
+    }
+    h.a_ptr[s + 1] = h.a_ptr[s] + len * w;
+  }
+  h.a_col.assign(h.a_ptr[nslices], (int32_t)guard);
+  h.a_val.assign(h.a_ptr[nslices], 0.0);
+  for (int64_t s = 0; s < nslices; ++s)
+    for (int32_t j = 0; j < w; ++j) {
+      const int64_t k = s * w + j;
+      for (int64_t e = h.rp[k], t = 0; e < h.rp[k + 1]; ++e, ++t) {
+        const int64_t slot = h.a_ptr[s] + t * w + j;
+        h.a_col[slot] = h.ci[e];
+        h.a_val[slot] = h.av[e];
+      }
+    }
+
+  // Forward (rows of L): other-color entries in ascending column order, then
+  // same-block entries in ascending step.  Backward (rows of U = L^T):
+  // other-color entries in descending column order, then same-block entries
+  // in descending step.  Both orders put the column farthest from the
+  // diagonal first.
+  auto lower_index = [&](int64_t row, int64_t col) -> int64_t {
+    const int32_t *lo = h.lci.data() + h.lrp[row], *hi = h.lci.data() + h.lrp[row + 1];
+    const int32_t *f = std::lower_bound(lo, hi, (int32_t)col);
+    return h.lrp[row] + (f - lo);
+  };
+  h.lmap_f.assign(h.nnz_lower, 0);
+  h.lmap_b.assign(h.nnz_lower, 0);
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<int64_t> &optr = dir == 0 ? h.fo_ptr : h.bo_ptr;
+    std::vector<int64_t> &iptr = dir == 0 ? h.fi_ptr : h.bi_ptr;
+    std::vector<int32_t> &ocol = dir == 0 ? h.fo_col : h.bo_col;
+    std::vector<uint8_t> &im = dir == 0 ? h.fi_m : h.bi_m;
+    std::vector<int64_t> &lmap = dir == 0 ? h.lmap_f : h.lmap_b;
+    optr.assign(nslices + 1, 0);
+    iptr.assign(nslices + 1, 0);
+    // pass 1: slice lengths
+    for (int64_t s = 0; s < nslices; ++s) {
+      int64_t lo_max = 0, li_max = 0;
+      const int64_t tile = s / bs, tbeg = tile * tile_rows, tend = tbeg + tile_rows;
+      for (int32_t j = 0; j < w; ++j) {
+        const int64_t k = s * w + j;
+        int64_t lo = 0, li = 0;
+        for (int64_t e = h.rp[k]; e < h.rp[k + 1]; ++e) {
+          const int64_t c = h.ci[e];
+          if (dir == 0 ? c >= k : c <= k) continue;
+          if (c >= tbeg && c < tend) ++li; else ++lo;
+        }
+        lo_max = std::max(lo_max, lo);
+        li_max = std::max(li_max, li);
+      }
+      optr[s + 1] = optr[s] + lo_max * w;
+      iptr[s + 1] = iptr[s] + li_max * w;
+    }
+    ocol.assign(optr[nslices], (int32_t)guard);
+    im.assign(iptr[nslices], 0);
+    // pass 2: fill; padded same-block slots point at a step that is already
+    // final when the slot is read (step 0 forward, step bs-1 backward)
+    for (int64_t s = 0; s < nslices; ++s) {
+      const int64_t tile = s / bs, tbeg = tile * tile_rows, tend = tbeg + tile_rows;
+      const int64_t l = s % bs;
+      for (int64_t t = iptr[s]; t < iptr[s + 1]; ++t) im[t] = (uint8_t)(dir == 0 ? 0 : bs - 1);
+      for (int32_t j = 0; j < w; ++j) {
+        const int64_t k = s * w + j;
+        int64_t to = 0, ti = 0;
+        const int64_t e0 = h.rp[k], e1 = h.rp[k + 1];
+        for (int pass = 0; pass < 2; ++pass) {  // 0: other colors, 1: same block
+          for (int64_t q = 0; q < e1 - e0; ++q) {
+            const int64_t e = dir == 0 ? e0 + q : e1 - 1 - q;
+            const int64_t c = h.ci[e];
+            if (dir == 0 ? c >= k : c <= k) continue;
+            const bool same = c >= tbeg && c < tend;
+            if (same != (pass == 1)) continue;
+            // lower entry holding this coefficient: (k, c) forward, (c, k) backward
+            const int64_t le = dir == 0 ? lower_index(k, c) : lower_index(c, k);
+            if (!same) {
+              const int64_t slot = optr[s] + to * w + j;
+              ocol[slot] = (int32_t)c;
+              lmap[le] = slot;
+              ++to;
+            } else {
+              const int64_t m = (c - tbeg) / w;
+              if ((c - tbeg) % w != j || (dir == 0 ? m >= l : m <= l)) {
+                fail(err, "internal: same-block coupling off its lane", k, c);
+                return HBMC_ERR_INVALID_ARG;
+              }
+              const int64_t slot = iptr[s] + ti * w + j;
+              im[slot] = (uint8_t)m;
+              lmap[le] = -slot - 1;
+              ++ti;
+            }
+          }
+        }
+      }
+    }
+  }
+  return HBMC_OK;
+}
+
+}  // namespace hbmc

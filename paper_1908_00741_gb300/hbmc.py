@@ -1,0 +1,318 @@
+"""Python binding of libhbmc.so (ctypes): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts numpy arrays / torch tensors to pointers and status codes to
+exceptions.  Function names follow the C ABI in include/hbmc.h.
+
+If libhbmc.so has not been built, the first call raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libhbmc.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_NOT_SPD_PIVOT = 2
+ERR_BREAKDOWN = 3
+NOT_CONVERGED = 4
+ERR_TIMEOUT = 5
+ERR_CUDA = 6
+ERR_OOM = 7
+ERR_NOT_FACTORED = 8
+ERR_NO_DEVICE = 9
+
+BLOCK_ALGEBRAIC = 0
+BLOCK_BOXES = 1
+PREC_F64 = 0
+PREC_F32 = 1
+LOOP_GRAPH = 0
+LOOP_HOST = 1
+
+EXPORTED = [
+    "hbmc_default_options", "hbmc_build", "hbmc_destroy", "hbmc_last_error",
+    "hbmc_status_string", "hbmc_info", "hbmc_get_ordering", "hbmc_get_matrix",
+    "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
+    "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
+    "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar",
+]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("blocking", ctypes.c_int32), ("grid", ctypes.c_int64 * 3),
+                ("box", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
+                ("loop_mode", ctypes.c_int32), ("host_only", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("nnz_lower", ctypes.c_int64), ("bs", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("nc", ctypes.c_int32), ("nblocks", ctypes.c_int64), ("ntiles", ctypes.c_int64),
+                ("sell_entries_a", ctypes.c_int64), ("sell_entries_l", ctypes.c_int64),
+                ("sell_entries_u", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("factored", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HbmcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libhbmc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        sigs = {
+            "hbmc_default_options": (None, [P]),
+            "hbmc_build": (I32, [I64, P, P, P, I32, I32, P, P]),
+            "hbmc_destroy": (None, [P]),
+            "hbmc_last_error": (ctypes.c_char_p, [P]),
+            "hbmc_status_string": (ctypes.c_char_p, [I32]),
+            "hbmc_info": (I32, [P, P]),
+            "hbmc_get_ordering": (I32, [P, P, P, P, P]),
+            "hbmc_get_matrix": (I32, [P, P, P, P]),
+            "hbmc_set_stream": (I32, [P, P]),
+            "hbmc_set_precision": (I32, [P, I32]),
+            "hbmc_ic0": (I32, [P, D, P]),
+            "hbmc_get_factor": (I32, [P, P, P]),
+            "hbmc_precond": (I32, [P, P, P]),
+            "hbmc_iccg": (I32, [P, P, P, D, I64, P, P, P]),
+            "hbmc_iccg_host": (I32, [P, P, P, D, I64, P, P, P]),
+            "hbmc_residual_history": (I32, [P, P, I64, P]),
+            "hbmc_fwd_bar": (I32, [P, P, P]),
+            "hbmc_bwd_bar": (I32, [P, P, P]),
+            "hbmc_spmv_bar": (I32, [P, P, P]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _status_name(s):
+    try:
+        return load().hbmc_status_string(s).decode()
+    except Exception:  # library not loadable while formatting an error
+        return f"status {s}"
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t, n, name):
+    """Device pointer of a contiguous float64 CUDA tensor of length n."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be a contiguous float64 tensor of length {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclasses.dataclass
+class SolveResult:
+    status: int
+    iters: int
+    relres: float
+    true_relres: float
+
+    @property
+    def converged(self):
+        return self.status == OK
+
+
+class Context:
+    """An hbmc_ctx handle; frees the context when garbage collected."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+        self._lib = load()
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("context destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.hbmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status, allowed=(OK,)):
+        if status not in allowed:
+            raise HbmcError(status, self._lib.hbmc_last_error(self._h).decode())
+        return status
+
+    def info(self) -> dict:
+        inf = Info()
+        self.check(self._lib.hbmc_info(self.handle, ctypes.byref(inf)))
+        return inf.as_dict()
+
+
+def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
+               loop_mode=LOOP_GRAPH, host_only=False, device=-1, check_every=16) -> Context:
+    """hbmc_build on a CSR (workloads.CSR or any object with n, row_ptr, col, val)."""
+    lib = load()
+    opt = Options()
+    lib.hbmc_default_options(ctypes.byref(opt))
+    if box is not None:
+        grid = grid if grid is not None else A.grid
+        if grid is None:
+            raise ValueError("box blocking needs the grid dimensions")
+        opt.blocking = BLOCK_BOXES
+        opt.grid[:] = [int(g) for g in grid]
+        opt.box[:] = [int(b) for b in box]
+    opt.precision = precision
+    opt.loop_mode = loop_mode
+    opt.host_only = 1 if host_only else 0
+    opt.device = device
+    opt.check_every = check_every
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    v = np.ascontiguousarray(A.val, dtype=np.float64)
+    h = ctypes.c_void_p()
+    s = lib.hbmc_build(int(A.n), _np_ptr(rp), _np_ptr(ci), _np_ptr(v), int(bs), int(w),
+                       ctypes.byref(opt), ctypes.byref(h))
+    if s != OK:
+        raise HbmcError(s, lib.hbmc_last_error(None).decode())
+    return Context(h, int(A.n))
+
+
+def hbmc_info(ctx: Context) -> dict:
+    return ctx.info()
+
+
+def hbmc_get_ordering(ctx: Context):
+    """Returns (pi[n], color_ptr[nc+1], block_of[n], block_color[nblocks])."""
+    inf = ctx.info()
+    pi = np.empty(inf["n"], dtype=np.int64)
+    cp = np.empty(inf["nc"] + 1, dtype=np.int64)
+    bo = np.empty(inf["n"], dtype=np.int64)
+    bc = np.empty(max(inf["nblocks"], 1), dtype=np.int32)
+    ctx.check(ctx._lib.hbmc_get_ordering(ctx.handle, _np_ptr(pi), _np_ptr(cp), _np_ptr(bo), _np_ptr(bc)))
+    return pi, cp, bo, bc[: inf["nblocks"]]
+
+
+def hbmc_get_matrix(ctx: Context):
+    """Abar on the padded index space: (row_ptr, col, val)."""
+    inf = ctx.info()
+    nnz = inf["nnz"] + inf["n_pad"] - inf["n"]
+    rp = np.empty(inf["n_pad"] + 1, dtype=np.int64)
+    ci = np.empty(max(nnz, 1), dtype=np.int32)
+    v = np.empty(max(nnz, 1), dtype=np.float64)
+    ctx.check(ctx._lib.hbmc_get_matrix(ctx.handle, _np_ptr(rp), _np_ptr(ci), _np_ptr(v)))
+    return rp, ci[:nnz], v[:nnz]
+
+
+def hbmc_set_stream(ctx: Context, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    raw = None if stream is None else getattr(stream, "cuda_stream", stream)
+    ctx.check(ctx._lib.hbmc_set_stream(ctx.handle, ctypes.c_void_p(raw) if raw else None))
+
+
+def hbmc_set_precision(ctx: Context, precision: int) -> None:
+    ctx.check(ctx._lib.hbmc_set_precision(ctx.handle, int(precision)))
+
+
+def hbmc_ic0(ctx: Context, shift: float = 0.0):
+    """Returns (status, bad_row); raises on errors other than a bad pivot."""
+    bad = ctypes.c_int64(-1)
+    s = ctx._lib.hbmc_ic0(ctx.handle, float(shift), ctypes.byref(bad))
+    ctx.check(s, (OK, ERR_NOT_SPD_PIVOT))
+    return s, int(bad.value)
+
+
+def hbmc_get_factor(ctx: Context):
+    """(lower values aligned with hbmc_get_matrix, diagonal l_ii)."""
+    inf = ctx.info()
+    nnz = inf["nnz"] + inf["n_pad"] - inf["n"]
+    lo = np.empty(max(nnz, 1))
+    dg = np.empty(max(inf["n_pad"], 1))
+    ctx.check(ctx._lib.hbmc_get_factor(ctx.handle, _np_ptr(lo), _np_ptr(dg)))
+    return lo[:nnz], dg[: inf["n_pad"]]
+
+
+def hbmc_precond(ctx: Context, r, z) -> None:
+    ctx.check(ctx._lib.hbmc_precond(ctx.handle, _dev_ptr(r, ctx.n, "r"), _dev_ptr(z, ctx.n, "z")))
+
+
+def hbmc_iccg(ctx: Context, b, x, tol=1e-8, maxit=10000) -> SolveResult:
+    """Device tensors b, x (x: initial guess in, solution out)."""
+    it, rr, tr = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
+    s = ctx._lib.hbmc_iccg(ctx.handle, _dev_ptr(b, ctx.n, "b"), _dev_ptr(x, ctx.n, "x"),
+                           float(tol), int(maxit), ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tr))
+    ctx.check(s, (OK, NOT_CONVERGED, ERR_BREAKDOWN))
+    return SolveResult(s, int(it.value), float(rr.value), float(tr.value))
+
+
+def hbmc_iccg_host(ctx: Context, b: np.ndarray, x: np.ndarray, tol=1e-8, maxit=10000) -> SolveResult:
+    """Host numpy arrays b, x (float64, length n); x is overwritten."""
+    for name, a in (("b", b), ("x", x)):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != ctx.n:
+            raise ValueError(f"{name} must be a contiguous float64 array of length {ctx.n}")
+    it, rr, tr = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
+    s = ctx._lib.hbmc_iccg_host(ctx.handle, _np_ptr(b), _np_ptr(x), float(tol), int(maxit),
+                                ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tr))
+    ctx.check(s, (OK, NOT_CONVERGED, ERR_BREAKDOWN))
+    return SolveResult(s, int(it.value), float(rr.value), float(tr.value))
+
+
+def hbmc_residual_history(ctx: Context, cap: int = 100000) -> np.ndarray:
+    h = np.empty(max(cap, 1))
+    cnt = ctypes.c_int64(0)
+    ctx.check(ctx._lib.hbmc_residual_history(ctx.handle, _np_ptr(h), int(cap), ctypes.byref(cnt)))
+    return h[: cnt.value].copy()
+
+
+def _bar(fn, ctx, a, b):
+    n_pad = ctx.info()["n_pad"]
+    ctx.check(fn(ctx.handle, _dev_ptr(a, n_pad, "input"), _dev_ptr(b, n_pad, "output")))
+
+
+def hbmc_fwd_bar(ctx: Context, r, y) -> None:
+    _bar(ctx._lib.hbmc_fwd_bar, ctx, r, y)
+
+
+def hbmc_bwd_bar(ctx: Context, y, z) -> None:
+    _bar(ctx._lib.hbmc_bwd_bar, ctx, y, z)
+
+
+def hbmc_spmv_bar(ctx: Context, p, q) -> None:
+    _bar(ctx._lib.hbmc_spmv_bar, ctx, p, q)
