@@ -77,6 +77,12 @@ typedef struct hbmc_options {
                         touch no GPU (inspection and CPU tests) */
   int32_t device;    /* CUDA device ordinal; -1 = the current device */
   int32_t check_every; /* HBMC_LOOP_HOST: iterations between flag polls (default 16) */
+  int32_t sweep_tpb;   /* level-1 blocks per CUDA block in the substitution kernels;
+                          0 = automatic, else a power of two with sweep_tpb * w <= 256 */
+  int32_t sweep_kernel; /* substitution kernels: 0 = automatic (one warp per level-1 block
+                           when w = 32 and its runs fit in shared memory, else 1);
+                           1 = one CUDA block per level-1 block(s);
+                           2 = TMA-fed persistent warp-specialized kernels (w = 32) */
 } hbmc_options;
 
 /* Fills *opt with the defaults. */

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libhbmc.so")
 OBJDIR = os.path.join(PKG, "_build")
 
-SOURCES = ["build_host.cpp", "kernels.cu", "api.cu"]
+SOURCES = ["build_host.cpp", "kernels.cu", "sweep_warp.cu", "sweep_tma.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +32,7 @@ def nvcc() -> str:
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "hbmc.h")]
-    return [f for f in files if f.endswith((".cu", ".cpp", ".h"))]
+    return [f for f in files if f.endswith((".cu", ".cpp", ".h", ".cuh"))]
 
 
 def _stale() -> bool:

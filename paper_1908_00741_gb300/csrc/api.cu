@@ -147,6 +147,26 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dalloc(ctx, d.y, nv));
   TRY(dalloc(ctx, d.t, nv));
   TRY(dalloc(ctx, d.y32, nv));
+  CK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
+  while ((1 << d.lw) < d.w) ++d.lw;
+  hbmc::sweep_geometry(h, d, ctx->opt.sweep_tpb);
+  d.sweep_kernel = ctx->opt.sweep_kernel;
+  d.rec_ints = h.rec_ints;
+  if (h.ntiles > 0) {
+    TRY(dupload(ctx, d.rec_f, h.rec_f));
+    TRY(dupload(ctx, d.rec_b, h.rec_b));
+    TRY(dupload(ctx, d.rec_a, h.rec_a));
+  }
+  hbmc::plan_warp_kernels(h, d);
+  CK(hbmc::setup_warp_kernels());
+  if (d.sweep_kernel == 2) {
+    std::vector<int32_t> rf, rb;
+    hbmc::plan_tma(h, d.tma_f, d.tma_b, rf, rb);
+    if (!rf.empty()) TRY(dupload(ctx, d.tma_f.rec, rf));
+    if (!rb.empty()) TRY(dupload(ctx, d.tma_b.rec, rb));
+    d.use_tma = 1;
+    CK(hbmc::setup_tma_kernels(d));
+  }
   d.part_len = hbmc::partials_needed(d);
   TRY(dalloc(ctx, d.part, (size_t)d.part_len));
   TRY(dalloc(ctx, d.hist, (size_t)hbmc::kHistCap));
@@ -266,6 +286,7 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
   if (iters) *iters = r.iters;
   if (relres) *relres = r.relres;
   if (true_relres) *true_relres = r.true_relres;
+  if (r.timeout) return set_err(ctx, HBMC_ERR_TIMEOUT, "a bounded device-side wait ran out");
   switch (r.status) {
     case hbmc::ST_CONVERGED: return HBMC_OK;
     case hbmc::ST_MAXIT: return set_err(ctx, HBMC_NOT_CONVERGED, "maxit reached before the tolerance");
@@ -318,6 +339,10 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
   if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown loop mode");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 2)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be 0, 1 or 2");
+  if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_tpb must be 0 or a power of two with sweep_tpb * w <= 256");
   hbmc_ctx *ctx = nullptr;
   try {
     ctx = new hbmc_ctx();

@@ -1,0 +1,137 @@
+// Device helpers shared by the kernel translation units: deterministic
+// reductions, and thin wrappers over the sm_90+/sm_100+ PTX for mbarriers and
+// TMA bulk copies.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hbmc {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum, valid in thread 0.  FP64 arithmetic is scarce on
+// this GPU (about 2 FP64 operations per clock per SM), so the tree is built
+// to issue few FP64 warp instructions: every thread parks its value in
+// shared memory, one warp adds NT/32 values per lane, then a 5-step
+// butterfly finishes (NT/32 - 1 + 5 FP64 warp instructions per block).
+template <int NT>
+__device__ double block_sum(double v) {
+  __shared__ double red[NT];
+  __syncthreads();
+  red[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = red[threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < NT / 32; ++k) s += red[threadIdx.x + 32 * k];
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// Thread 0 stores the block's partial(s); returns true in every thread of
+// the last block of the grid to arrive.
+__device__ __forceinline__ bool publish(double *slot, const double *vals, int nv, unsigned *cnt, unsigned nblocks) {
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nv; ++k) slot[k] = vals[k];
+    __threadfence();
+    const unsigned t = atomicAdd(cnt, 1u);
+    s_last = (t == nblocks - 1);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// Sum of part[k * stride + off] for k < count, in a fixed order; valid in thread 0.
+template <int NT>
+__device__ double gather_partials(const double *part, int64_t count, int stride, int off) {
+  __threadfence();
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < count; k += NT) acc += __ldcg(part + k * stride + off);
+  return block_sum<NT>(acc);
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// Row kernels run a fixed grid (a few CUDA blocks per SM) and loop over the
+// rows with a grid stride, so each thread accumulates its dot-product terms
+// over several rows before the block reduction.
+#define FOR_ROWS(row, n) \
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < (n); row += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA bulk copy (PTX ISA 8.0+, sm_90 and later)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Makes barrier initialisation visible to the other threads and to the TMA unit.
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the given phase parity: false once `deadline_ns` of the
+// global timer has passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t deadline_ns) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() > deadline_ns) return false;
+  }
+  return true;
+}
+
+// 1-D bulk copy global -> shared memory of this CTA, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Named barrier over `count` threads (a multiple of 32).
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+}  // namespace hbmc

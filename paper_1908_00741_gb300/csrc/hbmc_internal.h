@@ -55,6 +55,15 @@ struct HostLayout {
   // lower entry e -> slot of l_ij in the forward layout (>= 0: fo slot,
   // < 0: fi slot -v-1) and in the backward layout (bo / bi likewise)
   std::vector<int64_t> lmap_f, lmap_b;
+
+  // Per level-1 block ("unit") records, rec_ints int32 each:
+  //   [0] o_len, [1] i_len, [2..3] o_begin, [4..5] i_begin (int64 halves),
+  //   [6 .. 6+bs] o_rel, [7+bs .. 7+2bs] i_rel
+  // o = the unit's run of other-color (or, for SpMV, all) entries, i = its
+  // same-block run; *_rel are the slice starts inside each run.
+  int32_t rec_ints = 0;
+  std::vector<int32_t> rec_f, rec_b, rec_a;
+  int64_t max_o_f = 0, max_i_f = 0, max_o_b = 0, max_i_b = 0, max_a = 0;
 };
 
 // Validates the CSR and computes every host-side structure.  Returns
@@ -70,7 +79,7 @@ struct Scalars {
   int status;  // 0 running, 1 converged, 2 maxit reached, 3 breakdown
   int done;    // nonzero: every further kernel of the solve returns at once
   int zero_x;  // b == 0: the solution is x = 0
-  int pad0;
+  int timeout;  // a bounded device-side wait ran out
   long long bad_row;  // IC(0): smallest failing padded row, or a large sentinel
   unsigned int cnt[8];        // last-block counters of the reductions
   const double *user_b;       // per-call vectors in the original ordering
@@ -80,11 +89,51 @@ struct Scalars {
 enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_BREAKDOWN = 3 };
 enum { CNT_RES = 0, CNT_PQ = 1, CNT_RR = 2, CNT_RZ = 3, CNT_TRUE = 4 };
 
+// Shared-memory stage layout of the TMA-fed substitution kernels (byte
+// offsets inside one stage) for one direction and one value type.
+struct TmaLayout {
+  uint32_t off_in = 0, off_dinv = 0, off_aux = 0, off_ocol = 0, off_oval = 0, off_ival = 0,
+           off_im = 0, stage_bytes = 0;
+  int stages = 0;       // 0: does not fit, use the plain kernels
+  int ctas_per_sm = 0;  // resident CUDA blocks per SM at this layout
+};
+
+// Shared memory of one warp in the warp-per-unit kernels (byte offsets), and
+// warps per CUDA block; wpb = 0 means the plan does not fit.
+struct WarpPlan {
+  uint32_t off_t = 0, off_d = 0, off_iv = 0, off_im = 0, warp_bytes = 0;
+  int wpb = 0;
+};
+
+struct TmaPlan {
+  int32_t *rec = nullptr;  // device: per level-1 block record
+  int rec_ints = 0;
+  int64_t max_o = 0, max_i = 0;
+  TmaLayout f64, f32;
+};
+
 // Device-side copy of the layouts.
 struct DeviceLayout {
   int64_t n = 0, n_pad = 0, nnz_lower = 0;
   int32_t bs = 1, w = 1, nc = 0;
   std::vector<int64_t> tile_ptr;  // host copy, for launch geometry
+
+  // sweep launch geometry: level-1 blocks per CUDA block, and the largest
+  // same-block coefficient run of one CUDA block (staged in shared memory
+  // when it fits)
+  int32_t sweep_tpb = 1;
+  int32_t sm_count = 1;  // streaming multiprocessors of the device
+  int32_t sweep_kernel = 0;  // 0 warp per unit, 1 block per unit, 2 TMA-fed (see hbmc_options)
+  int32_t use_tma = 0;   // substitutions through the TMA-fed kernels when their plan fits
+  TmaPlan tma_f, tma_b;
+  // warp-per-unit kernels: device records and shared-memory plans
+  int32_t rec_ints = 0;
+  int32_t *rec_f = nullptr, *rec_b = nullptr, *rec_a = nullptr;
+  int64_t max_i_f = 0, max_i_b = 0;
+  WarpPlan wp_f64_f, wp_f64_b, wp_f32_f, wp_f32_b, wp_spmv;
+  int32_t lw = 0;        // log2(w)
+  int64_t max_in_f = 0, max_in_b = 0;
+  int32_t in_smem_f = 0, in_smem_b = 0;
 
   int32_t *inv = nullptr, *pi = nullptr;
   int64_t *a_ptr = nullptr;

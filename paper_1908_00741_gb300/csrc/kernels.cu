@@ -1,20 +1,24 @@
 // CUDA kernels of the HBMC-ICCG solve (sm_103a) and the sequences that
 // enqueue them.
 //
-// Thread mapping of the substitutions (Section 4.2.2, Eqs. "BAMC3", "y2-2",
-// "y2-3"): one group of w consecutive threads per level-1 block, lane j owns
-// BMC block j of that level-1 block, and the bs steps run in order inside the
-// thread.  Step l of all w lanes touches w consecutive rows, so every slice
-// column of the SELL layout is one coalesced load.  Couplings to other colors
-// are independent of the step chain and are gathered for all bs steps first;
-// the chain itself only involves the lane's own earlier steps and runs out of
-// shared memory.
+// Substitutions (Section 4.2.2): a color is one launch (the n_c - 1 thread
+// synchronizations of Section 4.3.3 become kernel boundaries); its level-1
+// blocks are independent (Eq. "BAMC3") and each CUDA block takes whole
+// level-1 blocks.  Inside one, lane j owns BMC block j and the bs steps of
+// Eqs. "y2-2"/"y2-3" run in order, each step touching w consecutive rows, so
+// every slice column of the SELL layout is one coalesced load.  The
+// couplings to other colors (Eq. "for3") do not depend on the step chain and
+// are computed first with one thread per row; the chain itself only involves
+// the lane's own earlier steps and runs out of shared memory.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdint>
 
 #include "hbmc_internal.h"
+#include "device_util.cuh"
 #include "kernels.h"
 
 namespace hbmc {
@@ -22,54 +26,6 @@ namespace {
 
 constexpr int kRowThreads = 256;
 constexpr int kSweepThreads = 128;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic block sum (fixed butterfly and tree); valid in thread 0.
-template <int NT>
-__device__ double block_sum(double v) {
-  __shared__ double red[NT / 32];
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (wid == 0) {
-    s = lane < NT / 32 ? red[lane] : 0.0;
-    s = warp_sum(s);
-  }
-  return s;
-}
-
-// Thread 0 stores the block's partial(s); returns true in every thread of
-// the last block of the grid to arrive.
-__device__ bool publish(double *slot, const double *vals, int nv, unsigned *cnt, unsigned nblocks) {
-  __shared__ unsigned s_last;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < nv; ++k) slot[k] = vals[k];
-    __threadfence();
-    const unsigned t = atomicAdd(cnt, 1u);
-    s_last = (t == nblocks - 1);
-  }
-  __syncthreads();
-  return s_last != 0;
-}
-
-// Sum of part[k * stride + off] for k < count, in a fixed order; valid in thread 0.
-template <int NT>
-__device__ double gather_partials(const double *part, int64_t count, int stride, int off) {
-  __threadfence();
-  double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < count; k += NT) acc += __ldcg(part + k * stride + off);
-  return block_sum<NT>(acc);
-}
-
-__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
 // ---------------------------------------------------------------------------
 // Permutations (Section 3, Eq. "xbar": xbar = P x)
@@ -117,32 +73,33 @@ __global__ void k_narrow(const double *src, float *dst, int64_t n) {
 
 __device__ __forceinline__ double sell_row(const int64_t *__restrict__ a_ptr,
                                            const int32_t *__restrict__ a_col,
-                                           const double *__restrict__ a_val, int w, int64_t row,
-                                           const double *x) {
-  const int64_t s = row / w;
-  const int j = (int)(row - s * w);
+                                           const double *__restrict__ a_val, int w, int lw,
+                                           int64_t row, const double *x) {
+  const int64_t s = row >> lw;
+  const int j = (int)(row & (w - 1));
   const int64_t pe = a_ptr[s + 1];
   double acc = 0.0;
   for (int64_t p = a_ptr[s] + j; p < pe; p += w) acc = fma(a_val[p], __ldg(x + a_col[p]), acc);
   return acc;
 }
 
+
+
 // mode 0: initial residual r = b - A x with ||b||^2 and ||r||^2;
 // mode 1: true residual after the solve, ||b - A x||^2 only (t is scratch).
 template <int kMode>
 __global__ void __launch_bounds__(kRowThreads)
     k_residual(const int64_t *__restrict__ a_ptr, const int32_t *__restrict__ a_col,
-               const double *__restrict__ a_val, int w, int64_t n_pad, const double *b,
+               const double *__restrict__ a_val, int w, int lw, int64_t n_pad, const double *b,
                const double *x, double *r, double *part, Scalars *sc, double *hist) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double bb = 0.0, rr = 0.0;
-  if (row < n_pad) {
-    const double acc = sell_row(a_ptr, a_col, a_val, w, row, x);
+  FOR_ROWS(row, n_pad) {
+    const double acc = sell_row(a_ptr, a_col, a_val, w, lw, row, x);
     const double bi = b[row];
     const double ri = bi - acc;
     if (kMode == 0) r[row] = ri;
-    bb = bi * bi;
-    rr = ri * ri;
+    bb = fma(bi, bi, bb);
+    rr = fma(ri, ri, rr);
   }
   double v[2];
   v[0] = block_sum<kRowThreads>(bb);
@@ -184,15 +141,14 @@ __global__ void __launch_bounds__(kRowThreads)
 template <bool kDot>
 __global__ void __launch_bounds__(kRowThreads)
     k_spmv(const int64_t *__restrict__ a_ptr, const int32_t *__restrict__ a_col,
-           const double *__restrict__ a_val, int w, int64_t n_pad, const double *p, double *q,
-           double *part, Scalars *sc) {
+           const double *__restrict__ a_val, int w, int lw, int64_t n_pad, const double *p,
+           double *q, double *part, Scalars *sc) {
   if (kDot && sc->done) return;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double pq = 0.0;
-  if (row < n_pad) {
-    const double acc = sell_row(a_ptr, a_col, a_val, w, row, p);
+  FOR_ROWS(row, n_pad) {
+    const double acc = sell_row(a_ptr, a_col, a_val, w, lw, row, p);
     q[row] = acc;
-    pq = p[row] * acc;
+    if (kDot) pq = fma(p[row], acc, pq);
   }
   if (!kDot) return;
   double v = block_sum<kRowThreads>(pq);
@@ -219,13 +175,12 @@ __global__ void __launch_bounds__(kRowThreads)
     return;
   }
   const double alpha = sc->alpha;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double rr = 0.0;
-  if (row < n_pad) {
+  FOR_ROWS(row, n_pad) {
     x[row] = fma(alpha, p[row], x[row]);
     const double ri = fma(-alpha, q[row], r[row]);
     r[row] = ri;
-    rr = ri * ri;
+    rr = fma(ri, ri, rr);
   }
   double v = block_sum<kRowThreads>(rr);
   if (!publish(part + blockIdx.x, &v, 1, &sc->cnt[CNT_RR], gridDim.x)) return;
@@ -256,103 +211,176 @@ __global__ void __launch_bounds__(kRowThreads)
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(handle, 0);
     return;
   }
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n_pad) return;
-  p[row] = mode == 0 ? z[row] : fma(sc->beta, p[row], z[row]);
+  if (mode == 0) {
+    FOR_ROWS(row, n_pad) p[row] = z[row];
+  } else {
+    const double beta = sc->beta;
+    FOR_ROWS(row, n_pad) p[row] = fma(beta, p[row], z[row]);
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Forward substitution, one color (Eqs. "for2", "for3", "y2-2", "y2-3"):
-//   y_i = (r_i - sum_j l_ij y_j) * dinv_i
-// T: arithmetic of the factor and of the accumulation; Y: storage of y.
+// Substitutions, one color per launch.  A CUDA block holds tpb whole level-1
+// blocks (tpb * bs * w rows).  Forward, color c (Eqs. "for2", "for3"):
+//   phase 1, one thread per row:  t_i = r_i - sum_{j in earlier colors} l_ij y_j
+//            (q_c of Eq. "for3"; these gathers do not depend on the step chain)
+//   phase 2, lane j of each level-1 block, steps l = 1..bs (Eqs. "y2-2", "y2-3"):
+//            y_i = (t_i - sum_{m<l} l_{i,(m,j)} y_(m,j)) * dinv_i, all in shared memory
+//   phase 3, one thread per row: store y.
+// Backward, color c, colors n_c..1 and steps bs..1, with U = L^T.
+// The per-row term order (other colors first, then the same BMC block, each
+// farthest from the diagonal first) matches the oracle exactly.
 // ---------------------------------------------------------------------------
+constexpr int kTileThreads = 256;
+
+template <typename T>
+struct SweepArgs {
+  const int64_t *o_ptr, *i_ptr;
+  const int32_t *o_col;
+  const uint8_t *i_m;
+  const T *o_val, *i_val, *dinv;
+  int bs, w, lw, tpb, in_smem;
+  int64_t max_in, tile0, ntiles;
+};
+
+template <typename T>
+struct SweepSmem {
+  T *tv, *dv, *iv;
+  int32_t *ip;
+  uint8_t *im;
+};
+
+template <typename T>
+__device__ __forceinline__ SweepSmem<T> carve(unsigned char *raw, const SweepArgs<T> &a) {
+  SweepSmem<T> m;
+  const int cap = a.tpb * (a.bs << a.lw);
+  m.tv = reinterpret_cast<T *>(raw);
+  m.dv = m.tv + cap;
+  m.ip = reinterpret_cast<int32_t *>(m.dv + cap);
+  uintptr_t q = reinterpret_cast<uintptr_t>(m.ip + a.tpb * a.bs + 1);
+  q = (q + 15) & ~uintptr_t(15);
+  m.iv = reinterpret_cast<T *>(q);
+  m.im = reinterpret_cast<uint8_t *>(m.iv + (a.in_smem ? a.max_in : 0));
+  return m;
+}
+
+// Shared prologue: slice offsets of the same-block runs and, when they fit,
+// the runs themselves.  Returns the global offset of the block's first run.
+template <typename T>
+__device__ __forceinline__ int64_t stage_runs(const SweepArgs<T> &a, const SweepSmem<T> &m,
+                                              int64_t s_begin, int nsl) {
+  const int64_t ib0 = a.i_ptr[s_begin];
+  for (int k = threadIdx.x; k <= nsl; k += kTileThreads) m.ip[k] = (int32_t)(a.i_ptr[s_begin + k] - ib0);
+  if (a.in_smem) {
+    const int64_t cnt = a.i_ptr[s_begin + nsl] - ib0;
+    for (int64_t e = threadIdx.x; e < cnt; e += kTileThreads) {
+      m.iv[e] = a.i_val[ib0 + e];
+      m.im[e] = a.i_m[ib0 + e];
+    }
+  }
+  return ib0;
+}
+
 template <typename T, typename Y>
-__global__ void __launch_bounds__(kSweepThreads)
-    k_fwd(const int64_t *__restrict__ fo_ptr, const int32_t *__restrict__ fo_col,
-          const T *__restrict__ fo_val, const int64_t *__restrict__ fi_ptr,
-          const uint8_t *__restrict__ fi_m, const T *__restrict__ fi_val,
-          const T *__restrict__ dinv, const double *__restrict__ r, Y *y, int bs, int w,
-          int64_t tile0, int64_t ntiles, const Scalars *sc) {
-  extern __shared__ unsigned char smem_raw[];
-  T *ts = reinterpret_cast<T *>(smem_raw);  // [bs][blockDim]: t_l, then y_l
+__global__ void __launch_bounds__(kTileThreads)
+    k_fwd(const SweepArgs<T> a, const double *__restrict__ r, Y *y, const Scalars *sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t tl = g / w;
-  if (tl >= ntiles) return;
-  const int j = (int)(g - tl * w);
-  const int64_t s0 = (tile0 + tl) * bs;
-  const int nt = blockDim.x, me = threadIdx.x;
-  // couplings to earlier colors: independent of the step chain
-  for (int l = 0; l < bs; ++l) {
-    const int64_t s = s0 + l;
-    T acc = (T)r[s * w + j];
-    const int64_t pe = fo_ptr[s + 1];
-    for (int64_t p = fo_ptr[s] + j; p < pe; p += w) acc = fma(-fo_val[p], (T)y[fo_col[p]], acc);
-    ts[l * nt + me] = acc;
+  const SweepSmem<T> m = carve(smem_raw, a);
+  const int R = a.bs << a.lw;
+  const int64_t bt0 = a.tile0 + (int64_t)blockIdx.x * a.tpb;
+  const int ntl = (int)min((int64_t)a.tpb, a.tile0 + a.ntiles - bt0);
+  const int nrows = ntl * R;
+  const int64_t row0 = bt0 * R;
+  const int64_t ib0 = stage_runs(a, m, bt0 * a.bs, ntl * a.bs);
+#pragma unroll 4
+  for (int lr = threadIdx.x; lr < nrows; lr += kTileThreads) {
+    const int64_t row = row0 + lr;
+    const int64_t s = row >> a.lw;
+    const int j = (int)(row & (a.w - 1));
+    T acc = (T)r[row];
+    const int64_t pe = a.o_ptr[s + 1];
+    for (int64_t p = a.o_ptr[s] + j; p < pe; p += a.w) acc = fma(-a.o_val[p], (T)y[a.o_col[p]], acc);
+    m.tv[lr] = acc;
+    m.dv[lr] = a.dinv[row];
   }
-  // the bs-step chain of this lane's BMC block
-  for (int l = 0; l < bs; ++l) {
-    const int64_t s = s0 + l;
-    const int64_t row = s * w + j;
-    T acc = ts[l * nt + me];
-    const int64_t pe = fi_ptr[s + 1];
-    for (int64_t p = fi_ptr[s] + j; p < pe; p += w) acc = fma(-fi_val[p], ts[fi_m[p] * nt + me], acc);
-    const T yv = acc * dinv[row];
-    ts[l * nt + me] = yv;
-    y[row] = (Y)yv;
+  __syncthreads();
+  if (threadIdx.x < ntl * a.w) {
+    const int tl = threadIdx.x >> a.lw, j = threadIdx.x & (a.w - 1);
+    T *tt = m.tv + tl * R;
+    const T *dd = m.dv + tl * R;
+    for (int l = 0; l < a.bs; ++l) {
+      const int k = tl * a.bs + l;
+      T acc = tt[(l << a.lw) + j];
+      const int pe = m.ip[k + 1];
+      for (int p = m.ip[k] + j; p < pe; p += a.w) {
+        const int mm = a.in_smem ? m.im[p] : a.i_m[ib0 + p];
+        const T v = a.in_smem ? m.iv[p] : a.i_val[ib0 + p];
+        acc = fma(-v, tt[(mm << a.lw) + j], acc);
+      }
+      tt[(l << a.lw) + j] = acc * dd[(l << a.lw) + j];
+    }
   }
+  __syncthreads();
+#pragma unroll 4
+  for (int lr = threadIdx.x; lr < nrows; lr += kTileThreads) y[row0 + lr] = (Y)m.tv[lr];
 }
 
-// ---------------------------------------------------------------------------
-// Backward substitution, one color (Section 4.2.2, last paragraph):
-//   z_i = (y_i - sum_j l_ji z_j) * dinv_i, steps bs..1
-// Optionally accumulates r.z for the CG (dot_mode 1: initial rho, 2: rho and
-// beta inside the loop); the launch of the last color finishes the sum.
-// ---------------------------------------------------------------------------
+// dot_mode 1: initial rho = r.z; 2: rho and beta = rho_new / rho.  The launch
+// of the last color (color 1) finishes the sum over every color's partials.
 template <typename T, typename Y>
-__global__ void __launch_bounds__(kSweepThreads)
-    k_bwd(const int64_t *__restrict__ bo_ptr, const int32_t *__restrict__ bo_col,
-          const T *__restrict__ bo_val, const int64_t *__restrict__ bi_ptr,
-          const uint8_t *__restrict__ bi_m, const T *__restrict__ bi_val,
-          const T *__restrict__ dinv, const Y *__restrict__ yin, double *z,
-          const double *__restrict__ r, int bs, int w, int64_t tile0, int64_t ntiles,
+__global__ void __launch_bounds__(kTileThreads)
+    k_bwd(const SweepArgs<T> a, const Y *__restrict__ yin, double *z, const double *__restrict__ r,
           Scalars *sc, int dot_mode, double *part, int64_t part_off, int last_launch,
           int64_t part_total) {
-  extern __shared__ unsigned char smem_raw[];
-  T *ts = reinterpret_cast<T *>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t tl = g / w;
-  const bool active = tl < ntiles;
-  const int j = (int)(g - tl * w);
-  const int64_t s0 = (tile0 + tl) * bs;
-  const int nt = blockDim.x, me = threadIdx.x;
-  double rz = 0.0;
-  if (active) {
-    for (int l = 0; l < bs; ++l) {
-      const int64_t s = s0 + l;
-      T acc = (T)yin[s * w + j];
-      const int64_t pe = bo_ptr[s + 1];
-      for (int64_t p = bo_ptr[s] + j; p < pe; p += w) acc = fma(-bo_val[p], (T)z[bo_col[p]], acc);
-      ts[l * nt + me] = acc;
-    }
-    for (int l = bs - 1; l >= 0; --l) {
-      const int64_t s = s0 + l;
-      const int64_t row = s * w + j;
-      T acc = ts[l * nt + me];
-      const int64_t pe = bi_ptr[s + 1];
-      for (int64_t p = bi_ptr[s] + j; p < pe; p += w) acc = fma(-bi_val[p], ts[bi_m[p] * nt + me], acc);
-      const T zv = acc * dinv[row];
-      ts[l * nt + me] = zv;
-      z[row] = (double)zv;
-      if (dot_mode) rz = fma(r[row], (double)zv, rz);
+  const SweepSmem<T> m = carve(smem_raw, a);
+  const int R = a.bs << a.lw;
+  const int64_t bt0 = a.tile0 + (int64_t)blockIdx.x * a.tpb;
+  const int ntl = (int)min((int64_t)a.tpb, a.tile0 + a.ntiles - bt0);
+  const int nrows = ntl * R;
+  const int64_t row0 = bt0 * R;
+  const int64_t ib0 = stage_runs(a, m, bt0 * a.bs, ntl * a.bs);
+#pragma unroll 4
+  for (int lr = threadIdx.x; lr < nrows; lr += kTileThreads) {
+    const int64_t row = row0 + lr;
+    const int64_t s = row >> a.lw;
+    const int j = (int)(row & (a.w - 1));
+    T acc = (T)yin[row];
+    const int64_t pe = a.o_ptr[s + 1];
+    for (int64_t p = a.o_ptr[s] + j; p < pe; p += a.w) acc = fma(-a.o_val[p], (T)z[a.o_col[p]], acc);
+    m.tv[lr] = acc;
+    m.dv[lr] = a.dinv[row];
+  }
+  __syncthreads();
+  if (threadIdx.x < ntl * a.w) {
+    const int tl = threadIdx.x >> a.lw, j = threadIdx.x & (a.w - 1);
+    T *tt = m.tv + tl * R;
+    const T *dd = m.dv + tl * R;
+    for (int l = a.bs - 1; l >= 0; --l) {
+      const int k = tl * a.bs + l;
+      T acc = tt[(l << a.lw) + j];
+      const int pe = m.ip[k + 1];
+      for (int p = m.ip[k] + j; p < pe; p += a.w) {
+        const int mm = a.in_smem ? m.im[p] : a.i_m[ib0 + p];
+        const T v = a.in_smem ? m.iv[p] : a.i_val[ib0 + p];
+        acc = fma(-v, tt[(mm << a.lw) + j], acc);
+      }
+      tt[(l << a.lw) + j] = acc * dd[(l << a.lw) + j];
     }
   }
+  __syncthreads();
+  double rz = 0.0;
+  for (int lr = threadIdx.x; lr < nrows; lr += kTileThreads) {
+    const double zv = (double)m.tv[lr];
+    z[row0 + lr] = zv;
+    if (dot_mode) rz = fma(r[row0 + lr], zv, rz);
+  }
   if (!dot_mode) return;
-  double v = block_sum<kSweepThreads>(rz);
+  const double v = block_sum<kTileThreads>(rz);
   if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
   if (!last_launch) return;
-  // the last color's launch: all earlier colors' partials are complete
   __shared__ unsigned s_last;
   if (threadIdx.x == 0) {
     __threadfence();
@@ -361,7 +389,7 @@ __global__ void __launch_bounds__(kSweepThreads)
   }
   __syncthreads();
   if (!s_last) return;
-  const double rho_new = gather_partials<kSweepThreads>(part, part_total, 1, 0);
+  const double rho_new = gather_partials<kTileThreads>(part, part_total, 1, 0);
   if (threadIdx.x != 0) return;
   sc->cnt[CNT_RZ] = 0;
   sc->rho_new = rho_new;
@@ -454,8 +482,14 @@ __global__ void k_set_bad_row(Scalars *sc) {
 
 inline unsigned blocks_for(int64_t n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 
-template <typename T>
-size_t sweep_smem(int bs) { return (size_t)bs * kSweepThreads * sizeof(T); }
+// Grid of the row kernels: enough CUDA blocks to fill every SM a few times
+// over, never more than one row per thread.
+constexpr int kRowBlocksPerSm = 8;
+inline unsigned row_grid(const DeviceLayout &d) {
+  const unsigned full = blocks_for(d.n_pad, kRowThreads);
+  const unsigned cap = (unsigned)(d.sm_count * kRowBlocksPerSm);
+  return full < cap ? full : cap;
+}
 
 }  // namespace
 
@@ -463,24 +497,83 @@ size_t sweep_smem(int bs) { return (size_t)bs * kSweepThreads * sizeof(T); }
 // Enqueue sequences
 // ---------------------------------------------------------------------------
 
+constexpr int kSweepSmemCap = 200 * 1024;
+constexpr int64_t kRunSmemBytes = 64 * 1024;
+
 cudaError_t setup_kernels() {
   cudaError_t e = cudaSuccess;
-  const int f64 = (int)(kMaxBs * kSweepThreads * sizeof(double));
-  const int f32 = (int)(kMaxBs * kSweepThreads * sizeof(float));
-  if ((e = cudaFuncSetAttribute(k_fwd<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f64))) return e;
-  if ((e = cudaFuncSetAttribute(k_bwd<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f64))) return e;
-  if ((e = cudaFuncSetAttribute(k_fwd<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, f32))) return e;
-  if ((e = cudaFuncSetAttribute(k_bwd<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, f32))) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemCap))) return e;
+  if ((e = cudaFuncSetAttribute(k_bwd<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemCap))) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemCap))) return e;
+  if ((e = cudaFuncSetAttribute(k_bwd<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmemCap))) return e;
   return e;
+}
+
+// Level-1 blocks per CUDA block of the sweeps, and the longest same-block
+// run a CUDA block stages (forward and backward layouts).
+void sweep_geometry(const HostLayout &h, DeviceLayout &d, int tpb) {
+  const int R = h.bs * h.w;
+  d.sweep_tpb = tpb > 0 ? tpb : (R >= kTileThreads ? 1 : kTileThreads / R);
+  d.max_in_f = d.max_in_b = 0;
+  for (int c = 0; c < h.nc; ++c)
+    for (int64_t t = h.tile_ptr[c]; t < h.tile_ptr[c + 1]; t += d.sweep_tpb) {
+      const int64_t te = std::min<int64_t>(t + d.sweep_tpb, h.tile_ptr[c + 1]);
+      d.max_in_f = std::max(d.max_in_f, h.fi_ptr[te * h.bs] - h.fi_ptr[t * h.bs]);
+      d.max_in_b = std::max(d.max_in_b, h.bi_ptr[te * h.bs] - h.bi_ptr[t * h.bs]);
+    }
 }
 
 int64_t partials_needed(const DeviceLayout &d) {
   int64_t sweep = 0;
-  for (int c = 0; c < d.nc; ++c)
-    sweep += blocks_for((d.tile_ptr[c + 1] - d.tile_ptr[c]) * d.w, kSweepThreads);
-  const int64_t rows = 2 * (int64_t)blocks_for(d.n_pad, kRowThreads);
-  return (sweep > rows ? sweep : rows) + 64;
+  for (int c = 0; c < d.nc; ++c) sweep += (d.tile_ptr[c + 1] - d.tile_ptr[c] + d.sweep_tpb - 1) / d.sweep_tpb;
+  const int64_t rows = 2 * (int64_t)row_grid(d);
+  return std::max(std::max(std::max(sweep, rows), tma_partials_needed(d)), warp_partials_needed(d)) + 64;
 }
+
+namespace {
+
+template <typename T>
+SweepArgs<T> sweep_args(const DeviceLayout &d, bool fwd, int c) {
+  SweepArgs<T> a;
+  a.o_ptr = fwd ? d.fo_ptr : d.bo_ptr;
+  a.i_ptr = fwd ? d.fi_ptr : d.bi_ptr;
+  a.o_col = fwd ? d.fo_col : d.bo_col;
+  a.i_m = fwd ? d.fi_m : d.bi_m;
+  if constexpr (sizeof(T) == 8) {
+    a.o_val = (const T *)(fwd ? d.fo_val : d.bo_val);
+    a.i_val = (const T *)(fwd ? d.fi_val : d.bi_val);
+    a.dinv = (const T *)d.dinv;
+  } else {
+    a.o_val = (const T *)(fwd ? d.fo_val32 : d.bo_val32);
+    a.i_val = (const T *)(fwd ? d.fi_val32 : d.bi_val32);
+    a.dinv = (const T *)d.dinv32;
+  }
+  a.bs = d.bs;
+  a.w = d.w;
+  a.lw = 0;
+  while ((1 << a.lw) < d.w) ++a.lw;
+  a.tpb = d.sweep_tpb;
+  a.max_in = fwd ? d.max_in_f : d.max_in_b;
+  a.in_smem = a.max_in * (int64_t)(sizeof(T) + 1) <= kRunSmemBytes ? 1 : 0;
+  a.tile0 = d.tile_ptr[c];
+  a.ntiles = d.tile_ptr[c + 1] - d.tile_ptr[c];
+  return a;
+}
+
+template <typename T>
+size_t sweep_smem(const SweepArgs<T> &a) {
+  const size_t cap = (size_t)a.tpb * (a.bs << a.lw);
+  size_t b = 2 * cap * sizeof(T) + (size_t)(a.tpb * a.bs + 1) * sizeof(int32_t);
+  b = (b + 15) & ~size_t(15);
+  if (a.in_smem) b += (size_t)a.max_in * (sizeof(T) + 1);
+  return b;
+}
+
+unsigned sweep_grid(const DeviceLayout &d, int c) {
+  return (unsigned)((d.tile_ptr[c + 1] - d.tile_ptr[c] + d.sweep_tpb - 1) / d.sweep_tpb);
+}
+
+}  // namespace
 
 void enqueue_gather_in(const DeviceLayout &d, const double *src, double *dst, int which, cudaStream_t s) {
   k_gather_in<<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(src, dst, d.inv, d.n_pad, d.sc, which);
@@ -499,46 +592,48 @@ void enqueue_narrow(const double *src, float *dst, int64_t n, cudaStream_t s) {
 }
 
 void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s) {
+  if (warp_spmv_usable(d)) return enqueue_spmv_warp(d, p, q, dot, s);
   if (dot)
-    k_spmv<true><<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(d.a_ptr, d.a_col, d.a_val, d.w, d.n_pad, p, q, d.part, d.sc);
+    k_spmv<true><<<row_grid(d), kRowThreads, 0, s>>>(d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, p, q, d.part, d.sc);
   else
-    k_spmv<false><<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(d.a_ptr, d.a_col, d.a_val, d.w, d.n_pad, p, q, d.part, d.sc);
+    k_spmv<false><<<row_grid(d), kRowThreads, 0, s>>>(d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, p, q, d.part, d.sc);
 }
 
 // Forward sweep over all colors: y (F64) or y32 (F32) from r.
 void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
+  if (warp_usable(d, true, prec)) return enqueue_fwd_warp(d, prec, r, check_done, s);
+  if (tma_usable(d, true, prec)) return enqueue_fwd_tma(d, prec, r, check_done, s);
   const Scalars *sc = check_done ? d.sc : nullptr;
   for (int c = 0; c < d.nc; ++c) {
-    const int64_t t0 = d.tile_ptr[c], nt = d.tile_ptr[c + 1] - t0;
-    const unsigned grid = blocks_for(nt * d.w, kSweepThreads);
-    if (prec == HBMC_PREC_F64)
-      k_fwd<double, double><<<grid, kSweepThreads, sweep_smem<double>(d.bs), s>>>(
-          d.fo_ptr, d.fo_col, d.fo_val, d.fi_ptr, d.fi_m, d.fi_val, d.dinv, r, d.y, d.bs, d.w, t0, nt, sc);
-    else
-      k_fwd<float, float><<<grid, kSweepThreads, sweep_smem<float>(d.bs), s>>>(
-          d.fo_ptr, d.fo_col, d.fo_val32, d.fi_ptr, d.fi_m, d.fi_val32, d.dinv32, r, d.y32, d.bs, d.w, t0, nt, sc);
+    if (prec == HBMC_PREC_F64) {
+      const SweepArgs<double> a = sweep_args<double>(d, true, c);
+      k_fwd<double, double><<<sweep_grid(d, c), kTileThreads, sweep_smem(a), s>>>(a, r, d.y, sc);
+    } else {
+      const SweepArgs<float> a = sweep_args<float>(d, true, c);
+      k_fwd<float, float><<<sweep_grid(d, c), kTileThreads, sweep_smem(a), s>>>(a, r, d.y32, sc);
+    }
   }
 }
 
 // Backward sweep over all colors (n_c..1): z from y / y32; dot_mode 0: no
 // dot, 1: initial rho = r.z, 2: rho and beta.
 void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s) {
+  if (warp_usable(d, false, prec)) return enqueue_bwd_warp(d, prec, r, dot_mode, check_done, s);
+  if (tma_usable(d, false, prec)) return enqueue_bwd_tma(d, prec, r, dot_mode, check_done, s);
   Scalars *sc = check_done || dot_mode ? d.sc : nullptr;
   int64_t total = 0;
-  for (int c = 0; c < d.nc; ++c) total += blocks_for((d.tile_ptr[c + 1] - d.tile_ptr[c]) * d.w, kSweepThreads);
+  for (int c = 0; c < d.nc; ++c) total += sweep_grid(d, c);
   int64_t off = 0;
   for (int c = d.nc - 1; c >= 0; --c) {
-    const int64_t t0 = d.tile_ptr[c], nt = d.tile_ptr[c + 1] - t0;
-    const unsigned grid = blocks_for(nt * d.w, kSweepThreads);
+    const unsigned grid = sweep_grid(d, c);
     const int last = c == 0;
-    if (prec == HBMC_PREC_F64)
-      k_bwd<double, double><<<grid, kSweepThreads, sweep_smem<double>(d.bs), s>>>(
-          d.bo_ptr, d.bo_col, d.bo_val, d.bi_ptr, d.bi_m, d.bi_val, d.dinv, d.y, d.z, r, d.bs, d.w,
-          t0, nt, sc, dot_mode, d.part, off, last, total);
-    else
-      k_bwd<float, float><<<grid, kSweepThreads, sweep_smem<float>(d.bs), s>>>(
-          d.bo_ptr, d.bo_col, d.bo_val32, d.bi_ptr, d.bi_m, d.bi_val32, d.dinv32, d.y32, d.z, r,
-          d.bs, d.w, t0, nt, sc, dot_mode, d.part, off, last, total);
+    if (prec == HBMC_PREC_F64) {
+      const SweepArgs<double> a = sweep_args<double>(d, false, c);
+      k_bwd<double, double><<<grid, kTileThreads, sweep_smem(a), s>>>(a, d.y, d.z, r, sc, dot_mode, d.part, off, last, total);
+    } else {
+      const SweepArgs<float> a = sweep_args<float>(d, false, c);
+      k_bwd<float, float><<<grid, kTileThreads, sweep_smem(a), s>>>(a, d.y32, d.z, r, sc, dot_mode, d.part, off, last, total);
+    }
     off += grid;
   }
 }
@@ -548,29 +643,29 @@ void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode,
 void enqueue_init(const DeviceLayout &d, int prec, cudaStream_t s) {
   enqueue_gather_in(d, nullptr, d.b, 0, s);
   enqueue_gather_in(d, nullptr, d.x, 1, s);
-  k_residual<0><<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(
-      d.a_ptr, d.a_col, d.a_val, d.w, d.n_pad, d.b, d.x, d.r, d.part, d.sc, d.hist);
+  k_residual<0><<<row_grid(d), kRowThreads, 0, s>>>(
+      d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, d.b, d.x, d.r, d.part, d.sc, d.hist);
   enqueue_fwd(d, prec, d.r, true, s);
   enqueue_bwd(d, prec, d.r, 1, true, s);
-  k_update_p<<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 0, 0, 0);
+  k_update_p<<<row_grid(d), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 0, 0, 0);
 }
 
 // One CG iteration.
 void enqueue_body(const DeviceLayout &d, int prec, cudaStream_t s, bool use_cond,
                   cudaGraphConditionalHandle h) {
   enqueue_spmv(d, d.p, d.q, true, s);
-  k_update_xr<<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(
+  k_update_xr<<<row_grid(d), kRowThreads, 0, s>>>(
       d.n_pad, d.p, d.q, d.x, d.r, d.part, d.sc, d.hist, use_cond ? 1 : 0, h);
   enqueue_fwd(d, prec, d.r, true, s);
   enqueue_bwd(d, prec, d.r, 2, true, s);
-  k_update_p<<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 1, use_cond ? 1 : 0, h);
+  k_update_p<<<row_grid(d), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 1, use_cond ? 1 : 0, h);
 }
 
 // After the loop: x out, true residual.
 void enqueue_final(const DeviceLayout &d, cudaStream_t s) {
   enqueue_gather_out(d, d.x, nullptr, true, s);
-  k_residual<1><<<blocks_for(d.n_pad, kRowThreads), kRowThreads, 0, s>>>(
-      d.a_ptr, d.a_col, d.a_val, d.w, d.n_pad, d.b, d.x, d.t, d.part, d.sc, d.hist);
+  k_residual<1><<<row_grid(d), kRowThreads, 0, s>>>(
+      d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, d.b, d.x, d.t, d.part, d.sc, d.hist);
 }
 
 void enqueue_ic0(const DeviceLayout &d, double shift, cudaStream_t s) {

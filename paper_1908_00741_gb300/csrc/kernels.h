@@ -3,12 +3,36 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "hbmc_internal.h"
 
 namespace hbmc {
 
 cudaError_t setup_kernels();
+void sweep_geometry(const HostLayout &h, DeviceLayout &d, int tpb);
 int64_t partials_needed(const DeviceLayout &d);
+
+// Warp-per-unit kernels (sweep_warp.cu)
+void plan_warp_kernels(const HostLayout &h, DeviceLayout &d);
+cudaError_t setup_warp_kernels();
+bool warp_usable(const DeviceLayout &d, bool fwd, int prec);
+bool warp_spmv_usable(const DeviceLayout &d);
+int64_t warp_partials_needed(const DeviceLayout &d);
+void enqueue_fwd_warp(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
+void enqueue_bwd_warp(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                      cudaStream_t s);
+void enqueue_spmv_warp(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);
+
+// TMA-fed substitution kernels (sweep_tma.cu)
+void plan_tma(const HostLayout &h, TmaPlan &pf, TmaPlan &pb, std::vector<int32_t> &rec_f,
+              std::vector<int32_t> &rec_b);
+cudaError_t setup_tma_kernels(DeviceLayout &d);
+bool tma_usable(const DeviceLayout &d, bool fwd, int prec);
+int64_t tma_partials_needed(const DeviceLayout &d);
+void enqueue_fwd_tma(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
+void enqueue_bwd_tma(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                     cudaStream_t s);
 
 void enqueue_gather_in(const DeviceLayout &d, const double *src, double *dst, int which, cudaStream_t s);
 void enqueue_gather_out(const DeviceLayout &d, const double *src, double *dst, bool to_user, cudaStream_t s);

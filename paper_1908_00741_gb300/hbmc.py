@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
     _fields_ = [("blocking", ctypes.c_int32), ("grid", ctypes.c_int64 * 3),
                 ("box", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("host_only", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("sweep_tpb", ctypes.c_int32), ("sweep_kernel", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -187,7 +188,8 @@ class Context:
 
 
 def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
-               loop_mode=LOOP_GRAPH, host_only=False, device=-1, check_every=16) -> Context:
+               loop_mode=LOOP_GRAPH, host_only=False, device=-1, check_every=16,
+               sweep_tpb=0, sweep_kernel=0) -> Context:
     """hbmc_build on a CSR (workloads.CSR or any object with n, row_ptr, col, val)."""
     lib = load()
     opt = Options()
@@ -204,6 +206,8 @@ def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
     opt.host_only = 1 if host_only else 0
     opt.device = device
     opt.check_every = check_every
+    opt.sweep_tpb = sweep_tpb
+    opt.sweep_kernel = sweep_kernel
     rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     v = np.ascontiguousarray(A.val, dtype=np.float64)

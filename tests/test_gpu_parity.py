@@ -320,3 +320,61 @@ def test_full_size_poisson128(lib, orc, bs):
     assert res.status == H.OK and res.iters == ref.iters
     assert _rel(host(x), ref.x) <= 1e-12
     assert res.true_relres < 1.1e-8
+
+
+@pytest.mark.parametrize("tpb,w,bs", [(1, 32, 8), (2, 32, 8), (4, 32, 8), (8, 32, 8), (2, 32, 16),
+                                      (8, 8, 8), (32, 8, 4), (1, 16, 16), (4, 4, 2)])
+def test_sweep_geometry_variants_bitwise(lib, orc, tpb, w, bs):
+    """Any number of level-1 blocks per CUDA block gives the same bits."""
+    box = W.box_for_bs(bs)
+    A = W.poisson7(11)
+    ctx = H.hbmc_build(A, bs, w, box=box, sweep_tpb=tpb)
+    assert H.hbmc_ic0(ctx, 0.05)[0] == H.OK
+    an = orc.analyse(A, bs, w, box=box)
+    lval, ldiag, dinv, _ = orc.factor(an, 0.05)
+    r = np.random.default_rng(tpb).standard_normal(an.n_pad)
+    y_ref = orc.fwd(an.row_ptr, an.col, lval, dinv, r)
+    z_ref = orc.bwd(an.row_ptr, an.col, lval, dinv, y_ref)
+    y = torch.empty(an.n_pad, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(y)
+    H.hbmc_fwd_bar(ctx, dev(r), y)
+    H.hbmc_bwd_bar(ctx, dev(y_ref), z)
+    np.testing.assert_array_equal(host(y), y_ref)
+    np.testing.assert_array_equal(host(z), z_ref)
+
+
+@pytest.mark.parametrize("name,mk,bs,w,box", [c for c in CASES if c[3] == 32])
+@pytest.mark.parametrize("precision", [H.PREC_F64, H.PREC_F32])
+def test_sweep_kernel_variants_agree(lib, orc, name, mk, bs, w, box, precision):
+    """The warp-per-unit kernels (default for w = 32), the block-per-unit
+    kernels and the TMA-fed kernels compute the same bits, in both
+    precisions, and FP64 matches the oracle."""
+    A = mk()
+    outs = []
+    for sk in (0, 1, 2):
+        ctx = H.hbmc_build(A, bs, w, box=box, sweep_kernel=sk, precision=precision)
+        assert H.hbmc_ic0(ctx, 0.1)[0] == H.OK
+        n_pad = ctx.info()["n_pad"]
+        r = np.random.default_rng(11).standard_normal(n_pad)
+        y = torch.empty(n_pad, dtype=torch.float64, device="cuda")
+        z = torch.empty_like(y)
+        q = torch.empty_like(y)
+        H.hbmc_fwd_bar(ctx, dev(r), y)
+        H.hbmc_bwd_bar(ctx, y, z)
+        H.hbmc_spmv_bar(ctx, dev(r), q)
+        b, _ = W.rhs_from_solution(A, 0)
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        res = H.hbmc_iccg(ctx, dev(b), x)
+        outs.append((host(y), host(z), res.iters, host(x), host(q)))
+    assert all(o[2] > 0 for o in outs)
+    for o in outs[1:]:
+        for k in (0, 1, 4):  # substitutions and SpMV: identical term order, identical bits
+            np.testing.assert_array_equal(outs[0][k], o[k])
+        # the dot products reduce in kernel-specific orders: equal counts, x to 1e-12
+        assert outs[0][2] == o[2]
+        assert _rel(o[3], outs[0][3]) <= 1e-12
+    if precision == H.PREC_F64:
+        an = orc.analyse(A, bs, w, box=box)
+        lval, _, dinv, _ = orc.factor(an, 0.1)
+        np.testing.assert_array_equal(outs[0][0], orc.fwd(an.row_ptr, an.col, lval, dinv, r))
+        np.testing.assert_array_equal(outs[0][4], orc.spmv(an.row_ptr, an.col, an.val, r))
