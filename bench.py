@@ -1,0 +1,427 @@
+"""Benchmark: HBMC-ICCG time to a 1e-8 relative residual on one GB300.
+
+Workload (default): 3D 7-point Poisson on a 128^3 grid (2,097,152 unknowns,
+14,581,760 nonzeros, Dirichlet, natural order), BMC blocks = 2x2x2 boxes
+(bs = 8), w = 32, greedy block coloring (2 colors), b = A x* with
+x* ~ U(-1, 1), x0 = 0, tolerance 1e-8.  A step is one complete hbmc_iccg
+call: permute b in, the CG loop with both substitutions, permute x out and
+the true residual; the IC(0) factorization is timed separately.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the host cores instead (each step a bounded sample of the same solve, scaled
+to the full iteration count).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ICCG time to 1e-8 FP64 residual; fwd/bwd subst GB/s vs HBM roofline"
+TOL = 1e-8
+GRID = 128
+DEFAULT_BS = 8
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value, device="cpu"):
+    """Max of a float over all ranks (identity on one rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_traffic(kernel, source):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/traffic.json), or None when the kernel source changed since."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        sha = hashlib.sha1(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+        return rec["bytes_per_launch"] if rec.get("source_sha1") == sha else None
+    except Exception:
+        return None
+
+
+def subst_bytes(n, nnz_lower, s):
+    """Algorithmic bytes of one forward / backward substitution (compulsory
+    traffic: each nonzero of L once with its int32 column, dinv, the input
+    vector in and the result out; the backward sweep also reads r for the
+    fused r.z).  s = bytes per factor value."""
+    fwd = nnz_lower * (s + 4) + n * s + n * 8 + n * s
+    bwd = nnz_lower * (s + 4) + n * s + n * s + n * 8 + n * 8
+    return fwd, bwd
+
+
+def spmv_bytes(n, nnz):
+    return nnz * 12 + 2 * n * 8
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    from paper_1908_00741_gb300 import hbmc as H
+    from paper_1908_00741_gb300 import workloads as W
+
+    H.load()
+    bs = args.bs
+    P = W.poisson_problem(GRID, bs=bs)
+    A = P.A
+    prec = H.PREC_F32 if args.precision == "f32" else H.PREC_F64
+    t0 = time.perf_counter()
+    loop = H.LOOP_HOST if args.loop == "host" else H.LOOP_GRAPH
+    ctx = H.hbmc_build(A, bs, 32, box=P.box, precision=prec, device=local, loop_mode=loop)
+    build_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    H.hbmc_set_stream(ctx, stream)
+    b = torch.tensor(P.b, device="cuda")
+    x = torch.zeros_like(b)
+
+    # IC(0): warm then time
+    H.hbmc_ic0(ctx, 0.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, bad = H.hbmc_ic0(ctx, 0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert st == H.OK, bad
+    ic0_ms = e0.elapsed_time(e1)
+
+    def step():
+        x.zero_()
+        return H.hbmc_iccg(ctx, b, x, tol=TOL, maxit=10000)
+
+    for _ in range(args.warmup):
+        res = step()
+    assert res.status == H.OK, res
+    launches = ctx.info()["last_launches"]
+
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        total_launches = 0
+        for _ in range(args.steps):
+            res = step()
+            total_launches += ctx.info()["last_launches"]
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ms_total = ev[0].elapsed_time(ev[1])
+    ms_step = max_over_ranks(dist, ms_total / args.steps, "cuda")
+    iters = res.iters
+    true_relres = res.true_relres
+    err = float(np.max(np.abs(x.cpu().numpy() - P.x_star)) / np.max(np.abs(P.x_star)))
+
+    # e2e: same solve through the host-buffer entry point (H2D of b and x0,
+    # D2H of x inside the timed region), pinned host memory
+    bh = torch.tensor(P.b).pin_memory().numpy()
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(2):
+        xh[:] = 0.0
+        H.hbmc_iccg_host(ctx, bh, xh, tol=TOL)
+    torch.cuda.synchronize()
+    e2e = []
+    for _ in range(max(3, args.steps // 2)):
+        xh[:] = 0.0
+        t = time.perf_counter()
+        H.hbmc_iccg_host(ctx, bh, xh, tol=TOL)
+        e2e.append((time.perf_counter() - t) * 1e3)
+    e2e_ms = max_over_ranks(dist, statistics.median(e2e), "cuda")
+
+    # Per-phase device times of one CG iteration, CUDA events on this stream
+    # around `reps` back-to-back runs of the same kernels the solve runs
+    # (hbmc_profile_kernels), for the roofline figures.
+    inf = ctx.info()
+    nnz_l = inf["nnz_lower"]
+    kernel_ms = {}
+    for pname, pv in (("f64", H.PREC_F64), ("f32", H.PREC_F32)):
+        H.hbmc_set_precision(ctx, pv)
+        x.zero_()
+        H.hbmc_iccg(ctx, b, x, tol=TOL)
+        prof = H.hbmc_profile_kernels(ctx, 30)
+        kernel_ms[f"fwd_{pname}"] = prof["fwd"]
+        kernel_ms[f"bwd_{pname}"] = prof["bwd"]
+        if pv == prec:
+            kernel_ms["spmv"] = prof["spmv"]
+            kernel_ms["update_xr"] = prof["update_xr"]
+            kernel_ms["update_p"] = prof["update_p"]
+    H.hbmc_set_precision(ctx, prec)
+
+    peak, peak_kind = measured_peaks()
+    gbs = {}
+    for pname, s in (("f64", 8), ("f32", 4)):
+        fb, bb = subst_bytes(A.n, nnz_l, s)
+        gbs[f"fwd_{pname}"] = fb / (kernel_ms[f"fwd_{pname}"] * 1e-3) / 1e9
+        gbs[f"bwd_{pname}"] = bb / (kernel_ms[f"bwd_{pname}"] * 1e-3) / 1e9
+    sp_bytes = spmv_bytes(A.n, A.nnz)
+    gbs["spmv"] = sp_bytes / (kernel_ms["spmv"] * 1e-3) / 1e9
+    gbs["update_xr"] = 6 * A.n * 8 / (kernel_ms["update_xr"] * 1e-3) / 1e9
+    gbs["update_p"] = 3 * A.n * 8 / (kernel_ms["update_p"] * 1e-3) / 1e9
+
+    # dominant kernel of a solve: SpMV (the largest share in the launch list)
+    traffic = measured_traffic("spmv", "paper_1908_00741_gb300/csrc/sweep_warp.cu")
+    roofline = {"bound": "hbm", "kernel": "spmv (q = A p, fused p.q)", "achieved": round(gbs["spmv"], 1),
+                "peak": peak, "unit": "GB/s", "frac": round(gbs["spmv"] / peak, 4),
+                "traffic": traffic, "algorithmic_bytes": sp_bytes, "peak_source": peak_kind}
+    subst = {k: {"GB/s": round(v, 1), "frac": round(v / peak, 4), "ms": round(kernel_ms[k], 4)}
+             for k, v in gbs.items()}
+
+    variants = {}
+    if not args.no_variants:
+        for vbs in (8, 16, 32):
+            for vp in ("f64", "f32"):
+                if vbs == bs and vp == args.precision:
+                    continue
+                Pv = W.poisson_problem(GRID, bs=vbs) if vbs != bs else P
+                cv = H.hbmc_build(Pv.A, vbs, 32, box=Pv.box, device=local,
+                                  precision=H.PREC_F32 if vp == "f32" else H.PREC_F64)
+                H.hbmc_set_stream(cv, stream)
+                H.hbmc_ic0(cv)
+                bv = torch.tensor(Pv.b, device="cuda")
+                xv = torch.zeros_like(bv)
+                for _ in range(2):
+                    xv.zero_()
+                    rv = H.hbmc_iccg(cv, bv, xv, tol=TOL)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 5
+                a.record(stream)
+                for _ in range(reps):
+                    xv.zero_()
+                    rv = H.hbmc_iccg(cv, bv, xv, tol=TOL)
+                c.record(stream)
+                torch.cuda.synchronize()
+                variants[f"bs{vbs}_{vp}"] = {"ms": round(a.elapsed_time(c) / reps, 3), "iters": rv.iters,
+                                            "true_relres": rv.true_relres}
+                cv.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(P, iters, args.cpu_sample_iters)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": round(ms_step, 4), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"7-point Poisson {GRID}^3 ({A.n} unknowns, {A.nnz} nonzeros), "
+                               f"bs={bs} ({'x'.join(map(str, P.box))} boxes), w=32, "
+                               f"{args.precision.upper()} substitutions, tol {TOL:g}",
+                   "n": A.n, "nnz": A.nnz, "bs": bs, "w": 32, "colors": inf["nc"],
+                   "precision": args.precision, "parallelism": f"replicas{world}", "loop": args.loop,
+                   "l2": "inputs larger than L2 (device working set "
+                         f"{inf['device_bytes'] / 1e9:.2f} GB)"},
+        "iters": iters, "true_relres": true_relres, "max_rel_err_vs_xstar": err,
+        "ic0_ms": round(ic0_ms, 3), "build_s": round(build_s, 3),
+        "ms_per_iter": round(ms_step / max(iters, 1), 4),
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 2 * A.n * 8,
+                "d2h_bytes_per_step": A.n * 8},
+        "gpu_launches": int(total_launches), "launches_per_step": int(launches),
+        "roofline": roofline, "subst_roofline": subst, "variants": variants,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(P, gpu_iters, sample_iters):
+    """The oracle as it stands: single-threaded FP64 C, on this host.  Sample:
+    setup (blocking, coloring, reordering, IC(0)) plus `sample_iters` PCG
+    iterations; value = setup-free solve time scaled to the GPU's iteration
+    count."""
+    import oracle
+    t = time.perf_counter()
+    an = oracle.analyse(P.A, P.bs, P.w, box=P.box)
+    lval, _, dinv, bad = oracle.factor(an, 0.0)
+    setup_s = time.perf_counter() - t
+    t = time.perf_counter()
+    s = oracle.pcg(an, lval, dinv, P.b, tol=TOL, maxit=sample_iters)
+    dt = time.perf_counter() - t
+    per_iter = dt / max(s.iters, 1)
+    return {"value": round(per_iter * gpu_iters * 1e3, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"{s.iters} PCG iterations of the 128^3 solve ({dt:.2f} s, + {setup_s:.2f} s setup "
+                      f"not counted), scaled to {gpu_iters} iterations"}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1908_00741_gb300 import workloads as W
+
+    oracle.build()
+    P = W.poisson_problem(GRID, bs=args.bs)
+    an = oracle.analyse(P.A, P.bs, P.w, box=P.box)
+    lval, _, dinv, _ = oracle.factor(an, 0.0)
+    full_iters = args.ref_full_iters
+    sample = args.ref_sample_iters
+
+    def step():
+        t = time.perf_counter()
+        s = oracle.pcg(an, lval, dinv, P.b, tol=TOL, maxit=sample)
+        return (time.perf_counter() - t) / max(s.iters, 1) * full_iters * 1e3
+
+    for _ in range(args.warmup):
+        step()
+    vals = [step() for _ in range(args.steps)]
+    v = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"7-point Poisson {GRID}^3 ({P.A.n} unknowns), bs={args.bs}, w=32, "
+                               f"FP64, tol {TOL:g}", "bs": args.bs, "w": 32, "precision": "f64",
+                   "parallelism": "single-thread CPU oracle"},
+        "cpu_baseline": {"value": round(v, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: {sample} PCG iterations of the 128^3 solve, scaled to "
+                                   f"{full_iters} iterations"},
+        "e2e": {"value": round(v, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--bs", type=int, default=DEFAULT_BS)
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="graph: one CUDA graph per solve with a device-side while node; "
+                         "host: host-driven iterations (kernels visible to ncu)")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=40)
+    ap.add_argument("--ref-sample-iters", type=int, default=10)
+    ap.add_argument("--ref-full-iters", type=int, default=124)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -105,6 +105,8 @@ typedef struct hbmc_info_t {
   int32_t precision;
   int32_t factored;   /* 1 after a successful hbmc_ic0 */
   size_t device_bytes;      /* device memory held by the context */
+  int64_t last_iters;       /* iterations of the last hbmc_iccg call */
+  int64_t last_launches;    /* kernels launched by the last hbmc_iccg call */
 } hbmc_info_t;
 
 /*
@@ -243,6 +245,18 @@ hbmc_status hbmc_residual_history(const hbmc_ctx *ctx, double *hist, int64_t cap
 hbmc_status hbmc_fwd_bar(hbmc_ctx *ctx, const double *r_dev, double *y_dev);
 hbmc_status hbmc_bwd_bar(hbmc_ctx *ctx, const double *y_dev, double *z_dev);
 hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev);
+
+/*
+ * hbmc_profile_kernels - average device time (ms, CUDA events on the
+ * context's stream) of each phase of one CG iteration, each run `reps`
+ * times back to back on the context's own vectors: ms[0] forward
+ * substitution (all colors), ms[1] backward substitution with the fused r.z
+ * (all colors), ms[2] SpMV with the fused p.q, ms[3] x/r update with ||r||,
+ * ms[4] p update.  Call it after a solve (the vectors then hold data of the
+ * right scale); it leaves the context ready for the next solve.
+ * Synchronizes the stream.
+ */
+hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,7 @@ struct hbmc_ctx {
   double *stage_b = nullptr, *stage_x = nullptr;  // device staging for hbmc_iccg_host
   std::vector<void *> allocs;
   int64_t last_iters = 0;
+  int64_t last_launches = 0;
 };
 
 namespace {
@@ -283,6 +284,19 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
   CK(cudaStreamSynchronize(ctx->stream));
   const Scalars &r = *ctx->h_sc;
   ctx->last_iters = r.iters;
+  {
+    // init: 2 gathers, residual, n_c + n_c sweeps, p = z; per CG iteration:
+    // SpMV, x/r update, 2 n_c sweeps, p update; after: gather, residual.
+    // In graph mode the body runs `iters` times (at least once); in host
+    // mode it is enqueued in groups of check_every.
+    const int64_t nc = d.nc, per = 3 + 2 * nc;
+    int64_t passes = r.iters > 0 ? r.iters : 1;
+    if (ctx->opt.loop_mode == HBMC_LOOP_HOST) {
+      const int64_t every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+      passes = (passes + every - 1) / every * every;
+    }
+    ctx->last_launches = (4 + 2 * nc) + passes * per + 2;
+  }
   if (iters) *iters = r.iters;
   if (relres) *relres = r.relres;
   if (true_relres) *true_relres = r.true_relres;
@@ -431,6 +445,8 @@ hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info) {
   info->precision = ctx->precision;
   info->factored = ctx->factored ? 1 : 0;
   info->device_bytes = ctx->d.bytes;
+  info->last_iters = ctx->last_iters;
+  info->last_launches = ctx->last_launches;
   return HBMC_OK;
 }
 
@@ -618,6 +634,57 @@ hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev) {
   hbmc::enqueue_spmv(d, d.t, d.q, false, ctx->stream);
   CK(cudaMemcpyAsync(q_dev, d.q, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaGetLastError());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms) {
+  TRY(need_device(ctx));
+  if (!ms || reps < 1) return set_err(ctx, HBMC_ERR_INVALID_ARG, "bad arguments");
+  for (int k = 0; k < 5; ++k) ms[k] = 0.0;
+  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "no factor");
+  if (ctx->h.n == 0) return HBMC_OK;
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  cudaStream_t s = ctx->stream;
+  const int prec = ctx->precision;
+  // A scalar block that keeps every kernel running: not done, alpha = beta =
+  // 0 (the vector updates leave x, r, p unchanged), rho = 1, a large maxit.
+  Scalars sc;
+  std::memset(&sc, 0, sizeof sc);
+  sc.rho = 1.0;
+  sc.bnorm = 1.0;
+  sc.tol = 0.0;
+  sc.maxit = 1ll << 60;
+  sc.bad_row = LLONG_MAX;
+  *ctx->h_sc = sc;
+  CK(cudaMemcpyAsync(d.sc, ctx->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, s));
+  cudaEvent_t ev[2];
+  CK(cudaEventCreate(&ev[0]));
+  CK(cudaEventCreate(&ev[1]));
+  for (int k = 0; k < 5; ++k) {
+    auto run = [&]() {
+      switch (k) {
+        case 0: hbmc::enqueue_fwd(d, prec, d.r, true, s); break;
+        case 1: hbmc::enqueue_bwd(d, prec, d.r, 2, true, s); break;
+        case 2: hbmc::enqueue_spmv(d, d.p, d.q, true, s); break;
+        case 3: hbmc::enqueue_update_xr(d, s); break;
+        case 4: hbmc::enqueue_update_p(d, s); break;
+      }
+    };
+    for (int w = 0; w < 2; ++w) run();
+    CK(cudaEventRecord(ev[0], s));
+    for (int r = 0; r < reps; ++r) run();
+    CK(cudaEventRecord(ev[1], s));
+    CK(cudaEventSynchronize(ev[1]));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+    ms[k] = (double)t / reps;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  CK(cudaMemcpyAsync(ctx->h_sc, d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (ctx->h_sc->done) return set_err(ctx, HBMC_ERR_BREAKDOWN, "profiling run hit a breakdown; timings invalid");
   return HBMC_OK;
 }
 

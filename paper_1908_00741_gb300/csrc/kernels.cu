@@ -661,6 +661,14 @@ void enqueue_body(const DeviceLayout &d, int prec, cudaStream_t s, bool use_cond
   k_update_p<<<row_grid(d), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 1, use_cond ? 1 : 0, h);
 }
 
+void enqueue_update_xr(const DeviceLayout &d, cudaStream_t s) {
+  k_update_xr<<<row_grid(d), kRowThreads, 0, s>>>(d.n_pad, d.p, d.q, d.x, d.r, d.part, d.sc, d.hist, 0, 0);
+}
+
+void enqueue_update_p(const DeviceLayout &d, cudaStream_t s) {
+  k_update_p<<<row_grid(d), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 1, 0, 0);
+}
+
 // After the loop: x out, true residual.
 void enqueue_final(const DeviceLayout &d, cudaStream_t s) {
   enqueue_gather_out(d, d.x, nullptr, true, s);

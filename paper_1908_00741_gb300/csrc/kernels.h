@@ -44,6 +44,8 @@ void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode,
 void enqueue_init(const DeviceLayout &d, int prec, cudaStream_t s);
 void enqueue_body(const DeviceLayout &d, int prec, cudaStream_t s, bool use_cond, cudaGraphConditionalHandle h);
 void enqueue_final(const DeviceLayout &d, cudaStream_t s);
+void enqueue_update_xr(const DeviceLayout &d, cudaStream_t s);
+void enqueue_update_p(const DeviceLayout &d, cudaStream_t s);
 void enqueue_ic0(const DeviceLayout &d, double shift, cudaStream_t s);
 void enqueue_scatter_factor(const DeviceLayout &d, bool f32, cudaStream_t s);
 

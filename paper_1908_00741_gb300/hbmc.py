@@ -44,7 +44,7 @@ EXPORTED = [
     "hbmc_status_string", "hbmc_info", "hbmc_get_ordering", "hbmc_get_matrix",
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
-    "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar",
+    "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
 ]
 
 
@@ -62,7 +62,8 @@ class Info(ctypes.Structure):
                 ("nc", ctypes.c_int32), ("nblocks", ctypes.c_int64), ("ntiles", ctypes.c_int64),
                 ("sell_entries_a", ctypes.c_int64), ("sell_entries_l", ctypes.c_int64),
                 ("sell_entries_u", ctypes.c_int64), ("precision", ctypes.c_int32),
-                ("factored", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+                ("factored", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
+                ("last_iters", ctypes.c_int64), ("last_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -109,6 +110,7 @@ def load():
             "hbmc_fwd_bar": (I32, [P, P, P]),
             "hbmc_bwd_bar": (I32, [P, P, P]),
             "hbmc_spmv_bar": (I32, [P, P, P]),
+            "hbmc_profile_kernels": (I32, [P, I32, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -320,3 +322,13 @@ def hbmc_bwd_bar(ctx: Context, y, z) -> None:
 
 def hbmc_spmv_bar(ctx: Context, p, q) -> None:
     _bar(ctx._lib.hbmc_spmv_bar, ctx, p, q)
+
+
+PROFILE_PHASES = ("fwd", "bwd", "spmv", "update_xr", "update_p")
+
+
+def hbmc_profile_kernels(ctx: Context, reps: int = 20) -> dict:
+    """Average device ms per call of each phase of one CG iteration."""
+    out = np.zeros(5)
+    ctx.check(ctx._lib.hbmc_profile_kernels(ctx.handle, int(reps), _np_ptr(out)))
+    return dict(zip(PROFILE_PHASES, out.tolist()))
