@@ -258,6 +258,33 @@ hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev);
  */
 hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
 
+/*
+ * hbmc_spmv_dot_static - q = Abar p and p.q without allocating anything.
+ *
+ * The paper has no counterpart: this exists for callers that cannot
+ * allocate device memory when they need the product, such as code running
+ * while a stream is captured into a CUDA graph (cudaMalloc is not allowed
+ * then), programs whose device memory belongs entirely to another allocator,
+ * or loops that must not allocate after start-up.  It computes what the
+ * solver's SpMV computes (same bits in q), but keeps its reduction scratch
+ * in a fixed array of static device memory inside the library: 16 bytes plus
+ * 8192 doubles (64 KiB) per device, held by every GPU that loads the library
+ * until the process exits.
+ *
+ * p_dev, q_dev: device double[n_pad] in HBMC order (p may not alias q);
+ * pq_dev: device double receiving p.q.  Asynchronous on the context's
+ * stream.  Needs a context built with w = 32 and at most 32768 level-1
+ * blocks (n_pad <= 32768 * bs * 32); larger contexts get
+ * HBMC_ERR_INVALID_ARG with the limit in hbmc_last_error.  Calls no
+ * cudaMalloc or cudaFree.  The first call on a device looks up the static
+ * array's device address and sets a kernel attribute, so make that first
+ * call before any stream capture begins.  All calls on a device share the
+ * array: each clears it on its own stream before use, and calls whose
+ * kernels could overlap on the GPU race, so order them (one stream, or
+ * events).
+ */
+hbmc_status hbmc_spmv_dot_static(hbmc_ctx *ctx, const double *p_dev, double *q_dev, double *pq_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -689,3 +689,20 @@ hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms) {
 }
 
 }  // extern "C"
+
+namespace hbmc {
+
+// Read-only view of a context for entry points defined in other translation
+// units; returns false for a null or host-only context.
+bool ctx_view(hbmc_ctx *ctx, const DeviceLayout **d, cudaStream_t *stream, int *device,
+              bool *factored, std::string **err) {
+  if (!ctx || ctx->host_only) return false;
+  *d = &ctx->d;
+  *stream = ctx->stream;
+  *device = ctx->device;
+  *factored = ctx->factored;
+  *err = &ctx->err;
+  return true;
+}
+
+}  // namespace hbmc

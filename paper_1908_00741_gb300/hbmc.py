@@ -45,6 +45,7 @@ EXPORTED = [
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
+    "hbmc_spmv_dot_static",
 ]
 
 
@@ -111,6 +112,7 @@ def load():
             "hbmc_bwd_bar": (I32, [P, P, P]),
             "hbmc_spmv_bar": (I32, [P, P, P]),
             "hbmc_profile_kernels": (I32, [P, I32, P]),
+            "hbmc_spmv_dot_static": (I32, [P, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -332,3 +334,12 @@ def hbmc_profile_kernels(ctx: Context, reps: int = 20) -> dict:
     out = np.zeros(5)
     ctx.check(ctx._lib.hbmc_profile_kernels(ctx.handle, int(reps), _np_ptr(out)))
     return dict(zip(PROFILE_PHASES, out.tolist()))
+
+
+def hbmc_spmv_dot_static(ctx: Context, p, q, pq) -> None:
+    """q = Abar p and pq[0] = p.q (device tensors; p, q of length n_pad, pq of
+    length 1) using only the library's static scratch: for callers that must
+    not allocate device memory.  Asynchronous on the context's stream."""
+    n_pad = ctx.info()["n_pad"]
+    ctx.check(ctx._lib.hbmc_spmv_dot_static(ctx.handle, _dev_ptr(p, n_pad, "p"), _dev_ptr(q, n_pad, "q"),
+                                            _dev_ptr(pq, 1, "pq")))
