@@ -285,6 +285,72 @@ hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
  */
 hbmc_status hbmc_spmv_dot_static(hbmc_ctx *ctx, const double *p_dev, double *q_dev, double *pq_dev);
 
+/* ======================================================================
+ * Batched solver: many independent SPD systems in one set of launches.
+ *
+ * Each system is blocked, colored and HBMC-ordered on its own (Sections
+ * 4.1-4.2); the systems are then interleaved color by color, so one launch
+ * per color sweeps the level-1 blocks of every system (Eq. "BAMC3": blocks
+ * of one color are independent, and blocks of different systems never
+ * couple).  Every system keeps its own CG scalars and its own stopping test;
+ * its row arithmetic is the same as when it is solved alone.  w is 32.
+ * ====================================================================== */
+
+typedef struct hbmc_system {
+  int64_t n;                /* host CSR of one system (conventions as hbmc_build) */
+  const int64_t *row_ptr;
+  const int32_t *col;
+  const double *val;
+  int32_t blocking;         /* HBMC_BLOCK_ALGEBRAIC or HBMC_BLOCK_BOXES */
+  int64_t grid[3];          /* grid of this system for HBMC_BLOCK_BOXES */
+} hbmc_system;
+
+typedef struct hbmc_batch hbmc_batch; /* opaque */
+
+/* Build a batch of nsys >= 1 systems with block size bs (w = 32).  opt may
+ * be NULL; opt->box gives the box shape for systems that use box blocking;
+ * opt->precision, loop_mode and device apply to the batch. */
+hbmc_status hbmc_batch_build(int32_t nsys, const hbmc_system *systems, int32_t bs,
+                             const hbmc_options *opt, hbmc_batch **out);
+void hbmc_batch_destroy(hbmc_batch *b);
+const char *hbmc_batch_last_error(const hbmc_batch *b);
+
+/* Sizes: total unknowns (sum of n), padded rows, colors (max over systems),
+ * level-1 blocks; any pointer may be NULL. */
+hbmc_status hbmc_batch_info(const hbmc_batch *b, int64_t *n_total, int64_t *n_pad_total, int32_t *nc,
+                            int64_t *units);
+hbmc_status hbmc_batch_set_stream(hbmc_batch *b, void *stream);
+hbmc_status hbmc_batch_set_precision(hbmc_batch *b, int32_t precision);
+
+/* Shifted IC(0) of every system (Section 2, Eq. "ILU"; shift as in Section
+ * 5.1) with its own shift: shifts[s] (host, NULL = all 0, each > -1).
+ * bad_rows[s] (host, may be NULL) receives -1 or the first failing row of
+ * system s in its own original numbering.  Returns HBMC_ERR_NOT_SPD_PIVOT if
+ * any system failed; the others are factored and usable. */
+hbmc_status hbmc_batch_ic0(hbmc_batch *b, const double *shifts, int64_t *bad_rows);
+
+/* Solve every system to ||r_s|| / ||b_s|| < tol (Section 5.1 per system).
+ * b_dev, x_dev: device doubles, the systems' vectors concatenated in order
+ * (length sum of n); x_dev holds the initial guesses on entry.  Per-system
+ * outputs (host arrays of nsys, each may be NULL): iterations, final
+ * recurrence residual, true residual, status (an hbmc_status value), and
+ * solve_ms: device time from the start of the solve until that system met
+ * its tolerance.  Synchronizes.  Returns HBMC_OK when every system
+ * converged, else the first non-OK per-system status. */
+hbmc_status hbmc_batch_iccg(hbmc_batch *b, const double *b_dev, double *x_dev, double tol, int64_t maxit,
+                            int64_t *iters, double *relres, double *true_relres, int32_t *status,
+                            double *solve_ms);
+
+/* Autotuner: builds the batch for each block size in bs_candidates (box
+ * systems use the box shape of that size), factors with shift 0, solves b_dev
+ * twice and keeps the faster size.  ms[k] (may be NULL) receives the timed
+ * solve of candidate k (or -1 if it failed).  If cache_path is not NULL the
+ * choice is stored there under a fingerprint of the systems' sizes and
+ * reused without timing on the next call with the same fingerprint. */
+hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
+                                int32_t ncand, const hbmc_options *opt, const double *b_dev, double tol,
+                                int64_t maxit, const char *cache_path, int32_t *best_bs, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,10 @@ using hbmc::DeviceLayout;
 using hbmc::HostLayout;
 using hbmc::Scalars;
 
+namespace hbmc {
+hbmc_status finish_device_ctx(hbmc_ctx *ctx);
+}
+
 struct hbmc_ctx {
   HostLayout h;
   DeviceLayout d;
@@ -379,27 +383,7 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return s;
   }
   if (!ctx->host_only) {
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-      g_err = "no CUDA device";
-      delete ctx;
-      return HBMC_ERR_NO_DEVICE;
-    }
-    int dev = o.device;
-    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-    if (dev >= ndev) {
-      g_err = "device ordinal out of range";
-      delete ctx;
-      return HBMC_ERR_INVALID_ARG;
-    }
-    ctx->device = dev;
-    DeviceGuard guard(dev);
-    cudaError_t e = hbmc::setup_kernels();
-    if (e != cudaSuccess) {
-      s = cuda_err(ctx, e, "setup_kernels");
-    } else {
-      s = upload(ctx);
-    }
+    s = hbmc::finish_device_ctx(ctx);
     if (s != HBMC_OK) {
       g_err = ctx->err;
       hbmc_destroy(ctx);
@@ -691,6 +675,46 @@ hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms) {
 }  // extern "C"
 
 namespace hbmc {
+
+// Device half of context creation: pick the device, set kernel attributes
+// and upload the host layout.
+hbmc_status finish_device_ctx(hbmc_ctx *ctx) {
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return set_err(ctx, HBMC_ERR_NO_DEVICE, "no CUDA device");
+  int dev = ctx->opt.device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  if (dev >= ndev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "device ordinal out of range");
+  ctx->device = dev;
+  DeviceGuard guard(dev);
+  cudaError_t e = hbmc::setup_kernels();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "setup_kernels");
+  return upload(ctx);
+}
+
+// A device context around a host layout built elsewhere (the batched solver).
+hbmc_status make_ctx_from_layout(HostLayout &&h, const hbmc_options &opt, hbmc_ctx **out, std::string &err) {
+  *out = nullptr;
+  hbmc_ctx *ctx = nullptr;
+  try {
+    ctx = new hbmc_ctx();
+  } catch (...) {
+    err = "host allocation failed";
+    return HBMC_ERR_OOM;
+  }
+  ctx->opt = opt;
+  ctx->host_only = false;
+  ctx->precision = opt.precision;
+  ctx->h = std::move(h);
+  hbmc_status s = finish_device_ctx(ctx);
+  if (s != HBMC_OK) {
+    err = ctx->err;
+    hbmc_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return HBMC_OK;
+}
 
 // Read-only view of a context for entry points defined in other translation
 // units; returns false for a null or host-only context.

@@ -153,6 +153,45 @@ int32_t color_blocks(int64_t n, const int64_t *rp, const int32_t *ci, int64_t nb
 
 }  // namespace
 
+// Per-unit records (see HostLayout) from the slice pointer arrays.
+hbmc_status make_records(HostLayout &h, std::string &err) {
+  const int32_t bs = h.bs;
+  h.rec_ints = (8 + 2 * bs + 3) / 4 * 4;
+  for (int kind = 0; kind < 3; ++kind) {
+    const std::vector<int64_t> &op = kind == 0 ? h.fo_ptr : kind == 1 ? h.bo_ptr : h.a_ptr;
+    const std::vector<int64_t> *ip = kind == 0 ? &h.fi_ptr : kind == 1 ? &h.bi_ptr : nullptr;
+    std::vector<int32_t> &rec = kind == 0 ? h.rec_f : kind == 1 ? h.rec_b : h.rec_a;
+    int64_t max_o = 0, max_i = 0;
+    rec.assign((size_t)h.ntiles * h.rec_ints, 0);
+    for (int64_t u = 0; u < h.ntiles; ++u) {
+      int32_t *rc = rec.data() + (size_t)u * h.rec_ints;
+      const int64_t s0 = u * bs;
+      const int64_t ob = op[s0], olen = op[s0 + bs] - ob;
+      const int64_t ib = ip ? (*ip)[s0] : 0, ilen = ip ? (*ip)[s0 + bs] - ib : 0;
+      if (olen >= (int64_t(1) << 31) || ilen >= (int64_t(1) << 31)) {
+        fail(err, "a level-1 block holds too many entries", u);
+        return HBMC_ERR_INVALID_ARG;
+      }
+      max_o = std::max(max_o, olen);
+      max_i = std::max(max_i, ilen);
+      rc[0] = (int32_t)olen;
+      rc[1] = (int32_t)ilen;
+      rc[2] = (int32_t)(uint32_t)((uint64_t)ob & 0xffffffffu);
+      rc[3] = (int32_t)(uint32_t)((uint64_t)ob >> 32);
+      rc[4] = (int32_t)(uint32_t)((uint64_t)ib & 0xffffffffu);
+      rc[5] = (int32_t)(uint32_t)((uint64_t)ib >> 32);
+      for (int l = 0; l <= bs; ++l) {
+        rc[6 + l] = (int32_t)(op[s0 + l] - ob);
+        rc[7 + bs + l] = ip ? (int32_t)((*ip)[s0 + l] - ib) : 0;
+      }
+    }
+    if (kind == 0) { h.max_o_f = max_o; h.max_i_f = max_i; }
+    if (kind == 1) { h.max_o_b = max_o; h.max_i_b = max_i; }
+    if (kind == 2) h.max_a = max_o;
+  }
+  return HBMC_OK;
+}
+
 hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                        int32_t bs, int32_t w, const hbmc_options &opt, HostLayout &h,
                        std::string &err) {
@@ -387,41 +426,7 @@ hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const do
       }
     }
   }
-  // ---- per-unit records ------------------------------------------------------
-  h.rec_ints = (8 + 2 * bs + 3) / 4 * 4;
-  for (int kind = 0; kind < 3; ++kind) {
-    const std::vector<int64_t> &op = kind == 0 ? h.fo_ptr : kind == 1 ? h.bo_ptr : h.a_ptr;
-    const std::vector<int64_t> *ip = kind == 0 ? &h.fi_ptr : kind == 1 ? &h.bi_ptr : nullptr;
-    std::vector<int32_t> &rec = kind == 0 ? h.rec_f : kind == 1 ? h.rec_b : h.rec_a;
-    int64_t max_o = 0, max_i = 0;
-    rec.assign((size_t)h.ntiles * h.rec_ints, 0);
-    for (int64_t u = 0; u < h.ntiles; ++u) {
-      int32_t *rc = rec.data() + (size_t)u * h.rec_ints;
-      const int64_t s0 = u * bs;
-      const int64_t ob = op[s0], olen = op[s0 + bs] - ob;
-      const int64_t ib = ip ? (*ip)[s0] : 0, ilen = ip ? (*ip)[s0 + bs] - ib : 0;
-      if (olen >= (int64_t(1) << 31) || ilen >= (int64_t(1) << 31)) {
-        fail(err, "a level-1 block holds too many entries", u);
-        return HBMC_ERR_INVALID_ARG;
-      }
-      max_o = std::max(max_o, olen);
-      max_i = std::max(max_i, ilen);
-      rc[0] = (int32_t)olen;
-      rc[1] = (int32_t)ilen;
-      rc[2] = (int32_t)(uint32_t)((uint64_t)ob & 0xffffffffu);
-      rc[3] = (int32_t)(uint32_t)((uint64_t)ob >> 32);
-      rc[4] = (int32_t)(uint32_t)((uint64_t)ib & 0xffffffffu);
-      rc[5] = (int32_t)(uint32_t)((uint64_t)ib >> 32);
-      for (int l = 0; l <= bs; ++l) {
-        rc[6 + l] = (int32_t)(op[s0 + l] - ob);
-        rc[7 + bs + l] = ip ? (int32_t)((*ip)[s0 + l] - ib) : 0;
-      }
-    }
-    if (kind == 0) { h.max_o_f = max_o; h.max_i_f = max_i; }
-    if (kind == 1) { h.max_o_b = max_o; h.max_i_b = max_i; }
-    if (kind == 2) h.max_a = max_o;
-  }
-  return HBMC_OK;
+  return make_records(h, err);
 }
 
 }  // namespace hbmc

@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "hbmc.h"
 
 namespace hbmc {
@@ -72,6 +74,26 @@ hbmc_status build_host(int64_t n, const int64_t *row_ptr, const int32_t *col, co
                        int32_t bs, int32_t w, const hbmc_options &opt, HostLayout &h,
                        std::string &err);
 
+// Per-unit records of h from its slice pointer arrays (h.rec_*, h.max_*).
+hbmc_status make_records(HostLayout &h, std::string &err);
+
+// The batched solver's view of its systems (see batch_host.cpp).
+struct BatchMeta {
+  int32_t nsys = 0, nc = 0;
+  std::vector<int64_t> n, n_pad, orig0;   // per system; orig0[s] = first row of system s in
+                                          // the concatenated original-order vectors
+  std::vector<int32_t> nc_sys;
+  std::vector<int32_t> unit_sys;          // global level-1 block -> system
+  std::vector<int64_t> cu_start, cu_count;  // [s * nc + c]: system s's blocks of color c
+};
+
+hbmc_status build_batch_host(int32_t nsys, const hbmc_system *sys, int32_t bs, int32_t w,
+                             const hbmc_options &opt, HostLayout &g, BatchMeta &meta, std::string &err);
+
+// A device context around a prepared host layout, and a read-only view of a
+// context for entry points in other translation units.
+hbmc_status make_ctx_from_layout(HostLayout &&h, const hbmc_options &opt, hbmc_ctx **out, std::string &err);
+
 // Device scalars of one solve.
 struct Scalars {
   double rho, rho_new, beta, pq, alpha, rr, bb, bnorm, relres, tol, true_relres;
@@ -111,6 +133,10 @@ struct TmaPlan {
   int64_t max_o = 0, max_i = 0;
   TmaLayout f64, f32;
 };
+
+struct DeviceLayout;
+bool ctx_view(hbmc_ctx *ctx, const DeviceLayout **d, cudaStream_t *stream, int *device, bool *factored,
+              std::string **err);
 
 // Device-side copy of the layouts.
 struct DeviceLayout {

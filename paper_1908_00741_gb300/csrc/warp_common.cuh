@@ -1,0 +1,71 @@
+// Device helpers of the warp-per-unit kernels (one warp per level-1 block),
+// shared by the single-system and the batched solvers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_util.cuh"
+
+namespace hbmc {
+
+constexpr int kChunk = 8;
+
+__device__ __forceinline__ int64_t rec64(const int32_t *r, int k) {
+  return (int64_t)(((uint64_t)(uint32_t)r[k + 1] << 32) | (uint64_t)(uint32_t)r[k]);
+}
+
+// Deterministic sum over the CUDA block for any blockDim.x that is a
+// multiple of 32 (at most 1024); valid in thread 0.
+__device__ __forceinline__ double block_sum_rt(double v) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// ts[l] += sign * sum of the unit's run entries of slice l: v * src[col],
+// entries taken in run order (the per-row order fixed by the layout).  The
+// loads of kChunk entries are issued together before any is used.
+template <typename T, typename G, bool kNeg>
+__device__ __forceinline__ void run_accumulate(const int32_t *__restrict__ col, const T *__restrict__ val,
+                                               const G *src, int64_t beg, int len, const int32_t *rel,
+                                               T *ts, int lane) {
+  int l = 0;
+  for (int t0 = 0; t0 < len; t0 += kChunk * 32) {
+    int32_t c[kChunk];
+    T v[kChunk], g[kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      const int t = t0 + k * 32;
+      if (t < len) {
+        c[k] = col[beg + t + lane];
+        v[k] = val[beg + t + lane];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      const int t = t0 + k * 32;
+      if (t < len) g[k] = (T)src[c[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      const int t = t0 + k * 32;
+      if (t < len) {
+        while (t >= rel[l + 1]) ++l;
+        T *slot = ts + (l << 5) + lane;
+        *slot = fma(kNeg ? -v[k] : v[k], g[k], *slot);
+      }
+    }
+  }
+}
+
+}  // namespace hbmc

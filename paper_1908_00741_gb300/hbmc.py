@@ -46,6 +46,9 @@ EXPORTED = [
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
     "hbmc_spmv_dot_static",
+    "hbmc_batch_build", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
+    "hbmc_batch_set_stream", "hbmc_batch_set_precision", "hbmc_batch_ic0", "hbmc_batch_iccg",
+    "hbmc_batch_autotune",
 ]
 
 
@@ -113,6 +116,15 @@ def load():
             "hbmc_spmv_bar": (I32, [P, P, P]),
             "hbmc_profile_kernels": (I32, [P, I32, P]),
             "hbmc_spmv_dot_static": (I32, [P, P, P, P]),
+            "hbmc_batch_build": (I32, [I32, P, I32, P, P]),
+            "hbmc_batch_destroy": (None, [P]),
+            "hbmc_batch_last_error": (ctypes.c_char_p, [P]),
+            "hbmc_batch_info": (I32, [P, P, P, P, P]),
+            "hbmc_batch_set_stream": (I32, [P, P]),
+            "hbmc_batch_set_precision": (I32, [P, I32]),
+            "hbmc_batch_ic0": (I32, [P, P, P]),
+            "hbmc_batch_iccg": (I32, [P, P, P, D, I64, P, P, P, P, P]),
+            "hbmc_batch_autotune": (I32, [I32, P, P, I32, P, P, D, I64, ctypes.c_char_p, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -343,3 +355,166 @@ def hbmc_spmv_dot_static(ctx: Context, p, q, pq) -> None:
     n_pad = ctx.info()["n_pad"]
     ctx.check(ctx._lib.hbmc_spmv_dot_static(ctx.handle, _dev_ptr(p, n_pad, "p"), _dev_ptr(q, n_pad, "q"),
                                             _dev_ptr(pq, 1, "pq")))
+
+
+# --------------------------------------------------------------------------
+# Batched solver
+# --------------------------------------------------------------------------
+
+class System(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("blocking", ctypes.c_int32), ("grid", ctypes.c_int64 * 3)]
+
+
+def _systems(mats, use_boxes):
+    """ctypes array of hbmc_system for CSR matrices (box blocking on grid
+    matrices when use_boxes); returns (array, keep-alive list)."""
+    keep = []
+    arr = (System * len(mats))()
+    for k, A in enumerate(mats):
+        rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.col, dtype=np.int32)
+        v = np.ascontiguousarray(A.val, dtype=np.float64)
+        keep += [rp, ci, v]
+        arr[k].n = int(A.n)
+        arr[k].row_ptr = rp.ctypes.data
+        arr[k].col = ci.ctypes.data
+        arr[k].val = v.ctypes.data
+        if use_boxes and getattr(A, "grid", None) is not None:
+            arr[k].blocking = BLOCK_BOXES
+            arr[k].grid[:] = [int(g) for g in A.grid]
+        else:
+            arr[k].blocking = BLOCK_ALGEBRAIC
+    return arr, keep
+
+
+def _box_opts(bs, precision, loop_mode, device, check_every=16):
+    lib = load()
+    opt = Options()
+    lib.hbmc_default_options(ctypes.byref(opt))
+    shapes = {1: (1, 1, 1), 2: (1, 1, 2), 4: (1, 2, 2), 8: (2, 2, 2), 16: (2, 2, 4), 32: (2, 4, 4),
+              64: (4, 4, 4)}
+    opt.box[:] = list(shapes.get(bs, (1, 1, bs)))
+    opt.precision = precision
+    opt.loop_mode = loop_mode
+    opt.device = device
+    opt.check_every = check_every
+    return opt
+
+
+@dataclasses.dataclass
+class BatchResult:
+    status: int
+    iters: np.ndarray
+    relres: np.ndarray
+    true_relres: np.ndarray
+    statuses: np.ndarray
+    solve_ms: np.ndarray
+
+
+class Batch:
+    """An hbmc_batch handle (many independent systems solved together)."""
+
+    def __init__(self, handle, nsys, n_total, sizes):
+        self._h = handle
+        self.nsys = nsys
+        self.n_total = n_total
+        self.sizes = sizes
+        self._lib = load()
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("batch destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.hbmc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status, allowed=(OK,)):
+        if status not in allowed:
+            raise HbmcError(status, self._lib.hbmc_batch_last_error(self._h).decode())
+        return status
+
+    def info(self):
+        n, npad, nu = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        nc = ctypes.c_int32()
+        self.check(self._lib.hbmc_batch_info(self.handle, ctypes.byref(n), ctypes.byref(npad), ctypes.byref(nc),
+                                             ctypes.byref(nu)))
+        return {"n": n.value, "n_pad": npad.value, "nc": nc.value, "units": nu.value}
+
+
+def hbmc_batch_build(mats, bs, *, use_boxes=True, precision=PREC_F64, loop_mode=LOOP_GRAPH, device=-1,
+                     check_every=16) -> Batch:
+    """Batch of CSR systems (box blocking for grid matrices when use_boxes)."""
+    lib = load()
+    arr, keep = _systems(mats, use_boxes)
+    opt = _box_opts(bs, precision, loop_mode, device, check_every)
+    h = ctypes.c_void_p()
+    s = lib.hbmc_batch_build(len(mats), ctypes.cast(arr, ctypes.c_void_p), int(bs), ctypes.byref(opt),
+                             ctypes.byref(h))
+    if s != OK:
+        raise HbmcError(s, lib.hbmc_batch_last_error(None).decode())
+    del keep
+    sizes = [int(A.n) for A in mats]
+    return Batch(h, len(mats), sum(sizes), sizes)
+
+
+def hbmc_batch_set_stream(batch: Batch, stream) -> None:
+    raw = None if stream is None else getattr(stream, "cuda_stream", stream)
+    batch.check(batch._lib.hbmc_batch_set_stream(batch.handle, ctypes.c_void_p(raw) if raw else None))
+
+
+def hbmc_batch_set_precision(batch: Batch, precision: int) -> None:
+    batch.check(batch._lib.hbmc_batch_set_precision(batch.handle, int(precision)))
+
+
+def hbmc_batch_ic0(batch: Batch, shifts=None):
+    """Returns (status, bad_rows[nsys]); bad_rows[s] = -1 when system s factored."""
+    bad = np.full(batch.nsys, -1, dtype=np.int64)
+    sh = None if shifts is None else np.ascontiguousarray(shifts, dtype=np.float64)
+    s = batch._lib.hbmc_batch_ic0(batch.handle, _np_ptr(sh) if sh is not None else None, _np_ptr(bad))
+    batch.check(s, (OK, ERR_NOT_SPD_PIVOT))
+    return s, bad
+
+
+def hbmc_batch_iccg(batch: Batch, b, x, tol=1e-8, maxit=10000) -> BatchResult:
+    """Device tensors b, x (the systems' vectors concatenated)."""
+    k = batch.nsys
+    it = np.zeros(k, dtype=np.int64)
+    rr = np.zeros(k)
+    tr = np.zeros(k)
+    st = np.zeros(k, dtype=np.int32)
+    ms = np.zeros(k)
+    s = batch._lib.hbmc_batch_iccg(batch.handle, _dev_ptr(b, batch.n_total, "b"), _dev_ptr(x, batch.n_total, "x"),
+                                   float(tol), int(maxit), _np_ptr(it), _np_ptr(rr), _np_ptr(tr), _np_ptr(st),
+                                   _np_ptr(ms))
+    batch.check(s, (OK, NOT_CONVERGED, ERR_BREAKDOWN))
+    return BatchResult(s, it, rr, tr, st, ms)
+
+
+def hbmc_batch_autotune(mats, b, bs_candidates=(4, 8, 16, 32), *, use_boxes=True, precision=PREC_F32,
+                        tol=1e-8, maxit=10000, cache_path=None, device=-1):
+    """Pick the block size that solves the batch fastest; returns (best_bs, ms per candidate)."""
+    lib = load()
+    arr, keep = _systems(mats, use_boxes)
+    opt = _box_opts(8, precision, LOOP_GRAPH, device)
+    cand = np.ascontiguousarray(bs_candidates, dtype=np.int32)
+    ms = np.zeros(len(cand))
+    best = ctypes.c_int32(-1)
+    n_total = sum(int(A.n) for A in mats)
+    s = lib.hbmc_batch_autotune(len(mats), ctypes.cast(arr, ctypes.c_void_p), _np_ptr(cand), len(cand),
+                                ctypes.byref(opt), _dev_ptr(b, n_total, "b"), float(tol), int(maxit),
+                                cache_path.encode() if cache_path else None, ctypes.byref(best), _np_ptr(ms))
+    if s != OK:
+        raise HbmcError(s, lib.hbmc_batch_last_error(None).decode())
+    del keep
+    return int(best.value), ms

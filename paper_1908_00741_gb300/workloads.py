@@ -286,3 +286,22 @@ def vector_laplacian_problem(m: int, bs: int = 8, w: int = 32, seed: int = 3,
     A = permute_input(A, random_order(order_seed, A.n))
     b, xs = rhs_from_solution(A, rhs_seed)
     return Problem(f"veclap_{m}^3_bs{bs}", A, b, xs, bs, w, None)
+
+
+def batch_problems(nsys: int = 256, seed0: int = 1000, nmin: int = 16, nmax: int = 64):
+    """Uneven batch of SPD systems: system s (stream seed0 + s) draws a stencil
+    in {7, 27} with probability 1/2 each, an edge m ~ U{nmin..nmax} and sigma ~
+    U[0, 2]; its coefficients are smoothed lognormal (kappa stream
+    2*(seed0+s)+1), natural lexicographic order, b = A x* with x* ~ U(-1, 1)
+    (stream 2*(seed0+s)+2).  Returns a list of (A, b, x*)."""
+    out = []
+    for s in range(nsys):
+        seed = seed0 + s
+        u = uniform(seed, 3)
+        points = 7 if u[0] < 0.5 else 27
+        m = nmin + min(int(u[1] * (nmax - nmin + 1)), nmax - nmin)
+        sigma = 2.0 * u[2]
+        A = heterogeneous_stencil(m, points, sigma, 2 * seed + 1)
+        b, xs = rhs_from_solution(A, 2 * seed + 2)
+        out.append((A, b, xs))
+    return out
