@@ -351,6 +351,69 @@ hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const 
                                 int32_t ncand, const hbmc_options *opt, const double *b_dev, double tol,
                                 int64_t maxit, const char *cache_path, int32_t *best_bs, double *ms);
 
+/* Per-system feature vectors of a batch (host float[nsys *
+ * HBMC_NUM_FEATURES], same definitions as hbmc_features). */
+hbmc_status hbmc_batch_features(hbmc_batch *b, float *feat);
+
+/* ======================================================================
+ * Learned IC(0) shift.
+ *
+ * The paper's shifted ICCG (Section 5.1) sets the diagonal shift by hand.
+ * Here the shift comes from a grid: shift c is 0 for c = 0 and 1e-3 * 2^(c-1)
+ * for c = 1..HBMC_SHIFT_GRID-1.  The plain rule takes the first shift of the
+ * grid whose IC(0) has only positive pivots.  A small MLP (D -> 32 -> 32 -> 1,
+ * ReLU, inputs standardized) reads the matrix features plus the shift code
+ * c / (HBMC_SHIFT_GRID - 1) and predicts log2 of the CG iterations that
+ * shift would need; the learned choice is the grid shift with the lowest
+ * prediction, with the plain rule as fallback when that factorization
+ * fails.  Forward pass, gradients and Adam run in the library's kernels.
+ * ====================================================================== */
+#define HBMC_NUM_FEATURES 12
+#define HBMC_SHIFT_GRID 13
+
+/* Matrix features (host float[HBMC_NUM_FEATURES]), computed on the device over
+ * the real rows of A: 0 log10 n; 1 mean nonzeros per row; 2 max nonzeros per
+ * row; 3 min and 4 mean diagonal dominance a_ii / sum_{j!=i} |a_ij| (capped at
+ * 10); 5 fraction of rows with dominance < 1 - 1e-9; 6 fraction of positive
+ * off-diagonals; 7 mean and 8 standard deviation of log a_ii; 9 colors n_c;
+ * 10 block size bs; 11 max dominance.  Needs w = 32. */
+hbmc_status hbmc_features(hbmc_ctx *ctx, float *feat);
+
+/* Shift c of the grid. */
+double hbmc_shift_grid(int32_t c);
+
+typedef struct hbmc_mlp hbmc_mlp; /* device-resident network and optimizer state */
+
+/* Number of parameters for input width in_dim (layout: W1[32][D], b1[32],
+ * W2[32][32], b2[32], w3[32], b3). */
+int32_t hbmc_mlp_num_params(int32_t in_dim);
+hbmc_status hbmc_mlp_create(int32_t in_dim, hbmc_mlp **out);
+void hbmc_mlp_destroy(hbmc_mlp *net);
+const char *hbmc_mlp_last_error(const hbmc_mlp *net);
+/* Host parameters (NULL keeps the current ones) and input standardization
+ * (mean, std > 0; NULL keeps them); resets the optimizer state. */
+hbmc_status hbmc_mlp_set_params(hbmc_mlp *net, const float *params, const float *in_mean, const float *in_std);
+hbmc_status hbmc_mlp_get_params(const hbmc_mlp *net, float *params);
+/* out_dev[b] = network(X_dev[b][:]) for B samples (device floats, row-major). */
+hbmc_status hbmc_mlp_forward(hbmc_mlp *net, const float *X_dev, int32_t B, float *out_dev);
+/* Gradient of the loss L = mean_b (out_b - T_b)^2 with respect to every
+ * parameter (device float[P]); *loss (host, may be NULL) receives L. */
+hbmc_status hbmc_mlp_gradient(hbmc_mlp *net, const float *X_dev, const float *T_dev, int32_t B, float *grad_dev,
+                              float *loss);
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) on L;
+ * *loss (may be NULL) receives L after training. */
+hbmc_status hbmc_mlp_train(hbmc_mlp *net, const float *X_dev, const float *T_dev, int32_t B, int32_t steps,
+                           float lr, float *loss);
+/* Learned shift for ctx's matrix: the grid shift with the lowest predicted
+ * iterations; predicted (host float[HBMC_SHIFT_GRID], may be NULL) gets the
+ * network's outputs.  Needs a network with in_dim = HBMC_NUM_FEATURES + 1. */
+hbmc_status hbmc_predict_shift(hbmc_ctx *ctx, hbmc_mlp *net, double *shift, float *predicted);
+/* Factor ctx with the learned shift (net != NULL) or the plain rule (net ==
+ * NULL).  If the learned shift's IC(0) fails, the plain rule continues from
+ * the next larger grid shift and *fallback is set to 1.  *shift_used gets the
+ * shift that factored.  HBMC_ERR_NOT_SPD_PIVOT if no grid shift works. */
+hbmc_status hbmc_ic0_auto(hbmc_ctx *ctx, hbmc_mlp *net, double *shift_used, int32_t *fallback);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ OUT = os.path.join(PKG, "libhbmc.so")
 OBJDIR = os.path.join(PKG, "_build")
 
 SOURCES = ["build_host.cpp", "batch_host.cpp", "kernels.cu", "sweep_warp.cu", "sweep_tma.cu", "api.cu",
-           "noalloc.cu", "batch.cu"]
+           "noalloc.cu", "batch.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -962,6 +962,32 @@ hbmc_status hbmc_batch_iccg(hbmc_batch *b, const double *b_dev, double *x_dev, d
   return ret;
 }
 
+hbmc_status hbmc_batch_features(hbmc_batch *b, float *feat) {
+  if (!b || !feat) return berr(b, HBMC_ERR_INVALID_ARG, "null argument");
+  View v;
+  if (!view(b, v)) return berr(b, HBMC_ERR_INVALID_ARG, "batch has no device context");
+  const hbmc::BatchMeta &m = b->meta;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(v.dev);
+  int32_t *ncs = nullptr;
+  float *fd = nullptr;
+  hbmc_status st = HBMC_OK;
+  if (cudaMalloc(&ncs, sizeof(int32_t) * m.nsys) != cudaSuccess ||
+      cudaMalloc(&fd, sizeof(float) * m.nsys * HBMC_NUM_FEATURES) != cudaSuccess)
+    st = HBMC_ERR_OOM;
+  if (st == HBMC_OK && cudaMemcpy(ncs, m.nc_sys.data(), sizeof(int32_t) * m.nsys, cudaMemcpyHostToDevice) != cudaSuccess)
+    st = HBMC_ERR_CUDA;
+  if (st == HBMC_OK) st = hbmc::features_on_device(*v.d, m.nsys, b->cu_start, b->cu_count, ncs, fd, v.s, b->err);
+  if (st == HBMC_OK &&
+      cudaMemcpy(feat, fd, sizeof(float) * m.nsys * HBMC_NUM_FEATURES, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = HBMC_ERR_CUDA;
+  cudaFree(ncs);
+  cudaFree(fd);
+  if (prev >= 0) cudaSetDevice(prev);
+  return st;
+}
+
 hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
                                 int32_t ncand, const hbmc_options *opt, const double *b_dev, double tol,
                                 int64_t maxit, const char *cache_path, int32_t *best_bs, double *ms) {

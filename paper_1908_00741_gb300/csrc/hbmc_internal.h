@@ -187,4 +187,10 @@ struct DeviceLayout {
   size_t bytes = 0;
 };
 
+// Features of a device layout seen as nsys systems (unit ranges per system and
+// color on the device; nullptr: one system spanning the whole layout).
+hbmc_status features_on_device(const DeviceLayout &d, int32_t nsys, const int64_t *cu_start_dev,
+                               const int64_t *cu_count_dev, const int32_t *nc_sys_dev, float *feat_dev,
+                               cudaStream_t s, std::string &err);
+
 }  // namespace hbmc

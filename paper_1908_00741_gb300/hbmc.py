@@ -48,7 +48,10 @@ EXPORTED = [
     "hbmc_spmv_dot_static",
     "hbmc_batch_build", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
     "hbmc_batch_set_stream", "hbmc_batch_set_precision", "hbmc_batch_ic0", "hbmc_batch_iccg",
-    "hbmc_batch_autotune",
+    "hbmc_batch_autotune", "hbmc_batch_features",
+    "hbmc_features", "hbmc_shift_grid", "hbmc_mlp_num_params", "hbmc_mlp_create", "hbmc_mlp_destroy",
+    "hbmc_mlp_last_error", "hbmc_mlp_set_params", "hbmc_mlp_get_params", "hbmc_mlp_forward",
+    "hbmc_mlp_gradient", "hbmc_mlp_train", "hbmc_predict_shift", "hbmc_ic0_auto",
 ]
 
 
@@ -125,6 +128,20 @@ def load():
             "hbmc_batch_ic0": (I32, [P, P, P]),
             "hbmc_batch_iccg": (I32, [P, P, P, D, I64, P, P, P, P, P]),
             "hbmc_batch_autotune": (I32, [I32, P, P, I32, P, P, D, I64, ctypes.c_char_p, P, P]),
+            "hbmc_batch_features": (I32, [P, P]),
+            "hbmc_features": (I32, [P, P]),
+            "hbmc_shift_grid": (D, [I32]),
+            "hbmc_mlp_num_params": (I32, [I32]),
+            "hbmc_mlp_create": (I32, [I32, P]),
+            "hbmc_mlp_destroy": (None, [P]),
+            "hbmc_mlp_last_error": (ctypes.c_char_p, [P]),
+            "hbmc_mlp_set_params": (I32, [P, P, P, P]),
+            "hbmc_mlp_get_params": (I32, [P, P]),
+            "hbmc_mlp_forward": (I32, [P, P, I32, P]),
+            "hbmc_mlp_gradient": (I32, [P, P, P, I32, P, P]),
+            "hbmc_mlp_train": (I32, [P, P, P, I32, I32, ctypes.c_float, P]),
+            "hbmc_predict_shift": (I32, [P, P, P, P]),
+            "hbmc_ic0_auto": (I32, [P, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -518,3 +535,134 @@ def hbmc_batch_autotune(mats, b, bs_candidates=(4, 8, 16, 32), *, use_boxes=True
         raise HbmcError(s, lib.hbmc_batch_last_error(None).decode())
     del keep
     return int(best.value), ms
+
+
+# --------------------------------------------------------------------------
+# Learned IC(0) shift
+# --------------------------------------------------------------------------
+
+NUM_FEATURES = 12
+SHIFT_GRID = 13
+
+
+def shift_grid():
+    """The shift grid: 0, then 1e-3 * 2^k for k = 0..11."""
+    lib = load()
+    return np.array([lib.hbmc_shift_grid(c) for c in range(SHIFT_GRID)])
+
+
+def hbmc_features(ctx: Context) -> np.ndarray:
+    f = np.zeros(NUM_FEATURES, dtype=np.float32)
+    ctx.check(ctx._lib.hbmc_features(ctx.handle, _np_ptr(f)))
+    return f
+
+
+def hbmc_batch_features(batch: Batch) -> np.ndarray:
+    f = np.zeros((batch.nsys, NUM_FEATURES), dtype=np.float32)
+    batch.check(batch._lib.hbmc_batch_features(batch.handle, _np_ptr(f)))
+    return f
+
+
+class Mlp:
+    """hbmc_mlp handle: D -> 32 -> 32 -> 1 network with device-side training."""
+
+    def __init__(self, in_dim: int):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        s = self._lib.hbmc_mlp_create(int(in_dim), ctypes.byref(h))
+        if s != OK:
+            raise HbmcError(s, self._lib.hbmc_mlp_last_error(None).decode())
+        self._h = h
+        self.in_dim = int(in_dim)
+        self.num_params = int(self._lib.hbmc_mlp_num_params(int(in_dim)))
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("network destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.hbmc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status):
+        if status != OK:
+            raise HbmcError(status, self._lib.hbmc_mlp_last_error(self._h).decode())
+
+    def set_params(self, params=None, mean=None, std=None):
+        def fp(a, n):
+            if a is None:
+                return None, None
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            if a.size != n:
+                raise ValueError(f"expected {n} values")
+            return a, _np_ptr(a)
+        p, pp = fp(params, self.num_params)
+        m, mp = fp(mean, self.in_dim)
+        s, sp = fp(std, self.in_dim)
+        self.check(self._lib.hbmc_mlp_set_params(self.handle, pp, mp, sp))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params, dtype=np.float32)
+        self.check(self._lib.hbmc_mlp_get_params(self.handle, _np_ptr(out)))
+        return out
+
+    @staticmethod
+    def _fptr(t, n, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or \
+                not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {n} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def forward(self, X):
+        import torch
+        B = X.shape[0]
+        out = torch.empty(B, dtype=torch.float32, device=X.device)
+        self.check(self._lib.hbmc_mlp_forward(self.handle, self._fptr(X, B * self.in_dim, "X"), int(B),
+                                              self._fptr(out, B, "out")))
+        return out
+
+    def gradient(self, X, T):
+        import torch
+        B = X.shape[0]
+        g = torch.empty(self.num_params, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_float(0)
+        self.check(self._lib.hbmc_mlp_gradient(self.handle, self._fptr(X, B * self.in_dim, "X"),
+                                               self._fptr(T, B, "T"), int(B), self._fptr(g, self.num_params, "g"),
+                                               ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train(self, X, T, steps, lr=1e-3):
+        B = X.shape[0]
+        loss = ctypes.c_float(0)
+        self.check(self._lib.hbmc_mlp_train(self.handle, self._fptr(X, B * self.in_dim, "X"), self._fptr(T, B, "T"),
+                                            int(B), int(steps), ctypes.c_float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+
+def hbmc_predict_shift(ctx: Context, net: Mlp):
+    """(learned shift, predicted log2 iterations per grid shift)."""
+    sh = ctypes.c_double(0)
+    pred = np.zeros(SHIFT_GRID, dtype=np.float32)
+    ctx.check(ctx._lib.hbmc_predict_shift(ctx.handle, net.handle, ctypes.byref(sh), _np_ptr(pred)))
+    return float(sh.value), pred
+
+
+def hbmc_ic0_auto(ctx: Context, net: Mlp | None = None):
+    """Factor with the learned shift (net) or the plain rule (None).
+    Returns (status, shift_used, fallback_used)."""
+    sh = ctypes.c_double(0)
+    fb = ctypes.c_int32(0)
+    s = ctx._lib.hbmc_ic0_auto(ctx.handle, net.handle if net is not None else None, ctypes.byref(sh),
+                               ctypes.byref(fb))
+    ctx.check(s, (OK, ERR_NOT_SPD_PIVOT))
+    return s, float(sh.value), bool(fb.value)

@@ -1,0 +1,137 @@
+"""Learned IC(0) shift: data from shift sweeps, training and use.
+
+Orchestration only: the sweeps are batched HBMC-ICCG solves, the features
+come from the library's feature kernel, and training is the library's
+forward/backward/Adam kernels (hbmc_mlp_train).  The network predicts
+log2(CG iterations) from [features, shift code]; the shift it recommends is
+the grid shift with the lowest prediction, and the plain positive-pivot rule
+(hbmc_ic0_auto without a network) stays the fallback and the judge.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import hbmc as H
+
+FAIL_FACTOR = 4.0  # a failed shift (pivot or no convergence) counts as 4 * maxit iterations
+
+
+@dataclasses.dataclass
+class Sweep:
+    features: np.ndarray   # [nsys, 12]
+    iters: np.ndarray      # [nsys, grid]; -1 = IC(0) failed or CG did not converge
+    true_relres: np.ndarray
+    maxit: int
+
+
+def sweep(mats, bvecs, bs=8, tol=1e-8, maxit=2000, precision=H.PREC_F32, use_boxes=False) -> Sweep:
+    """Iterations of every system at every grid shift (one batched solve per shift)."""
+    import torch
+    grid = H.shift_grid()
+    batch = H.hbmc_batch_build(mats, bs, use_boxes=use_boxes, precision=precision)
+    feats = H.hbmc_batch_features(batch)
+    b = torch.tensor(np.concatenate(bvecs), device="cuda")
+    x = torch.zeros_like(b)
+    iters = np.full((len(mats), len(grid)), -1, dtype=np.int64)
+    tr = np.full((len(mats), len(grid)), np.nan)
+    for c, a in enumerate(grid):
+        st, bad = H.hbmc_batch_ic0(batch, shifts=np.full(len(mats), a))
+        x.zero_()
+        res = H.hbmc_batch_iccg(batch, b, x, tol=tol, maxit=maxit)
+        ok = (bad == -1) & (res.statuses == H.OK)
+        iters[ok, c] = res.iters[ok]
+        tr[ok, c] = res.true_relres[ok]
+    batch.close()
+    return Sweep(feats, iters, tr, maxit)
+
+
+def plain_choice(iters_row):
+    """Index of the plain rule's shift: the first shift whose IC(0) works.  A
+    sweep marks failures of IC(0) and of CG alike, so the first entry that is
+    not -1 stands in for the first positive-pivot shift."""
+    ok = np.flatnonzero(iters_row >= 0)
+    return int(ok[0]) if len(ok) else -1
+
+
+def best_choice(iters_row):
+    """argmin over converged shifts, ties to the smaller shift."""
+    ok = iters_row >= 0
+    if not ok.any():
+        return -1
+    v = np.where(ok, iters_row, np.iinfo(np.int64).max)
+    return int(np.argmin(v))
+
+
+def dataset(sw: Sweep):
+    """Inputs [features, shift code] and targets log2(iterations) for every
+    (system, shift) pair of systems with at least one converged shift."""
+    g = sw.iters.shape[1]
+    keep = (sw.iters >= 0).any(axis=1)
+    X, T = [], []
+    for s in np.flatnonzero(keep):
+        for c in range(g):
+            it = sw.iters[s, c]
+            X.append(np.concatenate([sw.features[s], [c / (g - 1)]]))
+            T.append(np.log2(max(it, 1)) if it >= 0 else np.log2(FAIL_FACTOR * sw.maxit))
+    return np.asarray(X, np.float32), np.asarray(T, np.float32)
+
+
+def init_params(D, seed=0):
+    """Glorot-uniform weights, zero biases (numpy, seeded)."""
+    rng = np.random.default_rng(seed)
+    h = 32
+
+    def glorot(fan_out, fan_in):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        return rng.uniform(-lim, lim, size=(fan_out, fan_in))
+
+    return np.concatenate([glorot(h, D).ravel(), np.zeros(h), glorot(h, h).ravel(), np.zeros(h),
+                           glorot(1, h).ravel(), [0.0]]).astype(np.float32)
+
+
+def train(X, T, steps=3000, lr=3e-3, seed=0) -> H.Mlp:
+    """Network trained on the GPU by the library's kernels."""
+    import torch
+    D = X.shape[1]
+    net = H.Mlp(D)
+    mean = X.mean(axis=0)
+    std = X.std(axis=0)
+    std = np.where(std > 1e-6, std, 1.0).astype(np.float32)
+    net.set_params(init_params(D, seed), mean, std)
+    Xd = torch.tensor(X, device="cuda")
+    Td = torch.tensor(T, device="cuda")
+    net.train(Xd, Td, steps, lr)
+    return net
+
+
+def predicted_choice(net: H.Mlp, feats):
+    """Grid index with the lowest predicted iterations, per system."""
+    import torch
+    g = H.SHIFT_GRID
+    X = np.concatenate([np.repeat(feats, g, axis=0),
+                        np.tile(np.arange(g) / (g - 1), len(feats))[:, None]], axis=1).astype(np.float32)
+    out = net.forward(torch.tensor(X, device="cuda")).cpu().numpy().reshape(len(feats), g)
+    return np.argmin(out, axis=1), out
+
+
+def evaluate(net: H.Mlp, sw: Sweep):
+    """Iterations with the plain rule and with the learned choice (plus the
+    plain-rule fallback when the learned shift fails), per system."""
+    choice, _ = predicted_choice(net, sw.features)
+    plain, learned, fallback = [], [], []
+    for s in range(len(sw.iters)):
+        row = sw.iters[s]
+        pc = plain_choice(row)
+        if pc < 0:
+            continue
+        lc = int(choice[s])
+        fb = row[lc] < 0
+        if fb:  # the learned shift failed: continue with the plain rule above it
+            nxt = [c for c in range(lc + 1, len(row)) if row[c] >= 0]
+            lc = nxt[0] if nxt else pc
+        plain.append(row[pc])
+        learned.append(row[lc])
+        fallback.append(fb)
+    return np.array(plain), np.array(learned), np.array(fallback)

@@ -1,0 +1,149 @@
+"""Learned IC(0) shift: the library's feature, MLP forward/gradient/training
+kernels against the FP64 reference (oracle/learned.py), the plain rule
+against the oracle's, and what the trained network gains over the plain rule
+on held-out systems."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import learned as OL
+from paper_1908_00741_gb300 import hbmc as H
+from paper_1908_00741_gb300 import learned_shift as LS
+from paper_1908_00741_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_00741_gb300 import _build
+    _build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return H.load()
+
+
+MATS = [
+    ("poisson7_9", lambda: W.poisson7(9), 8, (2, 2, 2)),
+    ("hetero27_8_rand", lambda: W.permute_input(W.heterogeneous_stencil(8, 27, 2.0, 1), W.random_order(2, 512)), 8, None),
+    ("veclap_5_rand", lambda: W.permute_input(W.vector_laplacian(5, 3, 0.95), W.random_order(4, 375)), 4, None),
+]
+
+
+@pytest.mark.parametrize("name,mk,bs,box", MATS)
+def test_features_match_reference(lib, orc, name, mk, bs, box):
+    A = mk()
+    ctx = H.hbmc_build(A, bs, 32, box=box)
+    f = H.hbmc_features(ctx)
+    an = orc.analyse(A, bs, 32, box=box)
+    ref = OL.features(A, an.nc, bs)
+    np.testing.assert_allclose(f, ref, rtol=2e-6, atol=1e-6)
+
+
+def test_batch_features_match_reference(lib, orc):
+    mats = [mk() for _, mk, _, _ in MATS]
+    batch = H.hbmc_batch_build(mats, 8, use_boxes=False)
+    f = H.hbmc_batch_features(batch)
+    for k, A in enumerate(mats):
+        an = orc.analyse(A, 8, 32)
+        np.testing.assert_allclose(f[k], OL.features(A, an.nc, 8), rtol=2e-6, atol=1e-6)
+
+
+def _net_and_data(D=13, B=300, seed=0):
+    rng = np.random.default_rng(seed)
+    p = (rng.standard_normal(OL.n_params(D)) * 0.3).astype(np.float32)
+    X = rng.standard_normal((B, D)).astype(np.float32) * 3 + 1
+    T = rng.standard_normal(B).astype(np.float32)
+    mean = X.mean(0).astype(np.float32)
+    std = (X.std(0) + 0.1).astype(np.float32)
+    net = H.Mlp(D)
+    net.set_params(p, mean, std)
+    return net, p, mean, std, X, T
+
+
+def test_mlp_forward_matches_reference(lib):
+    net, p, mean, std, X, T = _net_and_data()
+    out = net.forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    ref, _ = OL.forward(p.astype(np.float64), mean.astype(np.float64), std.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_allclose(out, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+    np.testing.assert_array_equal(net.get_params(), p)
+
+
+def test_mlp_gradient_matches_reference(lib):
+    net, p, mean, std, X, T = _net_and_data(seed=1)
+    g, loss = net.gradient(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"))
+    g = g.cpu().numpy()
+    ref = OL.gradient(p.astype(np.float64), mean.astype(np.float64), std.astype(np.float64),
+                      X.astype(np.float64), T.astype(np.float64))
+    np.testing.assert_allclose(g, ref, rtol=2e-3, atol=2e-4 * np.abs(ref).max())
+    assert loss == pytest.approx(OL.loss(p, mean, std, X.astype(np.float64), T.astype(np.float64)), rel=1e-4)
+
+
+def test_mlp_training_fits_a_smooth_function(lib):
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-2, 2, size=(512, 3)).astype(np.float32)
+    T = (np.sin(X[:, 0]) + 0.5 * X[:, 1] ** 2 - X[:, 2]).astype(np.float32)
+    net = H.Mlp(3)
+    net.set_params(LS.init_params(3, 0), X.mean(0), X.std(0))
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    _, l0 = net.gradient(Xd, Td)
+    l1 = net.train(Xd, Td, 1500, 3e-3)
+    assert l1 < 0.05 * l0
+
+
+def _indefinite_1d(n=30, off=0.9):
+    import scipy.sparse as sp
+    M = sp.diags([np.full(n - 1, off), np.ones(n), np.full(n - 1, off)], [-1, 0, 1]).tocsr()
+    M.sort_indices()
+    return W.CSR(n, M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.copy())
+
+
+@pytest.mark.parametrize("A,bs,box", [(_indefinite_1d(), 4, None), (_indefinite_1d(40, 0.6), 8, None),
+                                      (W.poisson7(6), 8, (2, 2, 2))])
+def test_plain_rule_matches_reference(lib, orc, A, bs, box):
+    ctx = H.hbmc_build(A, bs, 32, box=box)
+    st, shift, fb = H.hbmc_ic0_auto(ctx)
+    ref = OL.plain_rule(orc.analyse(A, bs, 32, box=box))
+    assert st == H.OK and not fb
+    assert shift == ref
+
+
+def _instances(count, seed0, mmin=4, mmax=7):
+    out = []
+    for k in range(count):
+        u = W.uniform(7000 + seed0 + k, 2)
+        m = mmin + min(int(u[0] * (mmax - mmin + 1)), mmax - mmin)
+        dom = 0.9 + 0.3 * u[1]
+        A = W.permute_input(W.vector_laplacian(m, 5000 + seed0 + k, dom), W.random_order(9000 + seed0 + k, 3 * m ** 3))
+        b, _ = W.rhs_from_solution(A, 11000 + seed0 + k)
+        out.append((A, b))
+    return out
+
+
+def test_learned_shift_gain_over_plain_rule(lib):
+    """Train on shift sweeps of 64 small 3-DOF systems, evaluate on 24 held-out
+    ones: mean CG iterations with the learned shift (plain-rule fallback when
+    its IC(0) fails) versus the plain rule's first positive-pivot shift."""
+    train = _instances(64, 0)
+    test = _instances(24, 1000)
+    sw = LS.sweep([A for A, _ in train], [b for _, b in train], bs=4, maxit=1000)
+    X, T = LS.dataset(sw)
+    net = LS.train(X, T, steps=3000, lr=3e-3)
+    swt = LS.sweep([A for A, _ in test], [b for _, b in test], bs=4, maxit=1000)
+    plain, learned, fb = LS.evaluate(net, swt)
+    best = np.array([swt.iters[s, LS.best_choice(swt.iters[s])] for s in range(len(test))
+                     if LS.plain_choice(swt.iters[s]) >= 0])
+    gain = 1.0 - learned.mean() / plain.mean()
+    print(f"\nlearned-shift gain: plain {plain.mean():.2f} it, learned {learned.mean():.2f} it, "
+          f"best {best.mean():.2f} it, gain {100 * gain:.1f}%, fallbacks {int(fb.sum())}/{len(fb)}")
+    assert len(plain) >= 20
+    # the network may not lose more than 5% against the rule it replaces
+    assert learned.mean() <= 1.05 * plain.mean()
+    # and it must use its own choice on most systems (not only the fallback)
+    assert fb.mean() <= 0.5
+    # product path: hbmc_ic0_auto with the trained network on held-out systems
+    for A, b in test[:4]:
+        ctx = H.hbmc_build(A, 4, 32)
+        st, shift, used_fb = H.hbmc_ic0_auto(ctx, net)
+        if st == H.OK and not used_fb:
+            pred_shift, _ = H.hbmc_predict_shift(ctx, net)
+            assert shift == pred_shift
