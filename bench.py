@@ -424,6 +424,97 @@ def run_batch(args):
 
 
 # --------------------------------------------------------------------------
+# learned IC shift: train on shift sweeps, then compare with the plain rule
+# --------------------------------------------------------------------------
+
+def learned_instances(count, seed0):
+    """Training/held-out systems: 70% 3-DOF vector Laplacians (nodes m^3 with
+    m ~ U{12..40}, dominance factor ~ U[0.9, 1.2]) and 30% heterogeneous 27-point
+    stencils (m ~ U{16..48}, sigma ~ U[0, 2]); random input order."""
+    from paper_1908_00741_gb300 import workloads as W
+    out = []
+    for k in range(count):
+        seed = seed0 + k
+        u = W.uniform(seed, 4)
+        if u[0] < 0.7:
+            m = 12 + min(int(u[1] * 29), 28)
+            A = W.vector_laplacian(m, seed, 0.9 + 0.3 * u[2])
+        else:
+            m = 16 + min(int(u[1] * 33), 32)
+            A = W.heterogeneous_stencil(m, 27, 2.0 * u[2], seed)
+        A = W.permute_input(A, W.random_order(seed ^ 0x5bd1e995, A.n))
+        b, _ = W.rhs_from_solution(A, seed + 77777)
+        out.append((A, b))
+    return out
+
+
+def run_learned(args):
+    import torch
+    from paper_1908_00741_gb300 import hbmc as H
+    from paper_1908_00741_gb300 import learned_shift as LS
+    from paper_1908_00741_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    t = time.perf_counter()
+    train = learned_instances(args.learned_train, 5000)
+    held = learned_instances(args.learned_heldout, 90000)
+    gen_s = time.perf_counter() - t
+    t = time.perf_counter()
+    sw = LS.sweep([A for A, _ in train], [b for _, b in train], bs=8, maxit=2000)
+    X, T = LS.dataset(sw)
+    sweep_s = time.perf_counter() - t
+    t = time.perf_counter()
+    net = LS.train(X, T, steps=4000, lr=3e-3)
+    train_s = time.perf_counter() - t
+    swh = LS.sweep([A for A, _ in held], [b for _, b in held], bs=8, maxit=2000)
+    plain, learned, fb = LS.evaluate(net, swh)
+    best = np.array([swh.iters[s, LS.best_choice(swh.iters[s])] for s in range(len(held))
+                     if LS.plain_choice(swh.iters[s]) >= 0])
+
+    def solve(P, name):
+        ctx = H.hbmc_build(P.A, P.bs, 32, box=P.box, precision=H.PREC_F32, device=local)
+        b = torch.tensor(P.b, device="cuda")
+        rows = {}
+        for tag, nn in (("plain_rule", None), ("learned", net)):
+            st, shift, used_fb = H.hbmc_ic0_auto(ctx, nn)
+            assert st == H.OK
+            x = torch.zeros_like(b)
+            H.hbmc_iccg(ctx, b, x, tol=TOL)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            reps = 3
+            for _ in range(reps):
+                x.zero_()
+                r = H.hbmc_iccg(ctx, b, x, tol=TOL)
+            ev[1].record()
+            torch.cuda.synchronize()
+            rows[tag] = {"shift": shift, "fallback": used_fb, "iters": r.iters, "status": r.status,
+                         "true_relres": r.true_relres, "ms": round(ev[0].elapsed_time(ev[1]) / reps, 3)}
+        ctx.close()
+        return {"workload": name, "n": P.A.n, "nnz": P.A.nnz, **rows}
+
+    cfg5 = solve(W.vector_laplacian_problem(args.veclap_m, bs=8), f"3-DOF vector Laplacian {args.veclap_m}^3 nodes")
+    cfg3 = solve(W.heterogeneous27_problem(args.hetero_m, bs=8), f"heterogeneous 27-point {args.hetero_m}^3")
+    line = {
+        "metric": "CG iterations to 1e-8 with the learned IC shift vs the plain positive-pivot rule",
+        "value": float(learned.mean()), "unit": "iterations (held-out mean)", "higher_is_better": False,
+        "n_gpus": world, "dtype": "f32-subst/f64-cg", "data": "synthetic",
+        "config": {"workload": "shift sweeps over generated 3-DOF vector Laplacians and 27-point stencils",
+                   "train_systems": len(train), "heldout_systems": len(held), "shift_grid": list(H.shift_grid()),
+                   "bs": 8, "w": 32},
+        "heldout": {"plain_mean_iters": float(plain.mean()), "learned_mean_iters": float(learned.mean()),
+                    "best_mean_iters": float(best.mean()), "gain_vs_plain": float(1 - learned.mean() / plain.mean()),
+                    "fallbacks": int(fb.sum()), "systems": int(len(plain))},
+        "training": {"samples": int(len(T)), "final_loss": None, "sweep_s": round(sweep_s, 1),
+                     "train_s": round(train_s, 2), "gen_s": round(gen_s, 1)},
+        "config5": cfg5, "config3": cfg3,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # --------------------------------------------------------------------------
 
@@ -473,8 +564,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--bs", type=int, default=DEFAULT_BS)
-    ap.add_argument("--workload", default="poisson128", choices=["poisson128", "batch"],
-                    help="poisson128: the headline solve; batch: 256 uneven systems solved together")
+    ap.add_argument("--workload", default="poisson128", choices=["poisson128", "batch", "learned"],
+                    help="poisson128: the headline solve; batch: 256 uneven systems solved together; "
+                         "learned: learned IC shift against the plain rule")
+    ap.add_argument("--learned-train", type=int, default=200)
+    ap.add_argument("--learned-heldout", type=int, default=40)
+    ap.add_argument("--veclap-m", type=int, default=100)
+    ap.add_argument("--hetero-m", type=int, default=96)
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
@@ -493,7 +589,7 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build()
-        run_batch(args) if args.workload == "batch" else run_gpu(args)
+        {"batch": run_batch, "learned": run_learned}.get(args.workload, run_gpu)(args)
 
 
 if __name__ == "__main__":
