@@ -80,9 +80,14 @@ typedef struct hbmc_options {
   int32_t sweep_tpb;   /* level-1 blocks per CUDA block in the substitution kernels;
                           0 = automatic, else a power of two with sweep_tpb * w <= 256 */
   int32_t sweep_kernel; /* substitution kernels: 0 = automatic (one warp per level-1 block
-                           when w = 32 and its runs fit in shared memory, else 1);
+                           when w = 32 and its runs fit in shared memory -- right-hand side,
+                           dinv and same-block runs staged by bulk copy when bs is 4 or 8 --
+                           else 1);
                            1 = one CUDA block per level-1 block(s);
-                           2 = TMA-fed persistent warp-specialized kernels (w = 32) */
+                           2 = TMA-fed persistent warp-specialized kernels (w = 32);
+                           3 = one warp per level-1 block reading its runs with plain loads,
+                               and SpMV one warp per level-1 block too (w = 32).
+                           SpMV runs one thread per row except with 3. */
 } hbmc_options;
 
 /* Fills *opt with the defaults. */

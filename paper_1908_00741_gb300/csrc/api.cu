@@ -164,6 +164,10 @@ hbmc_status upload(hbmc_ctx *ctx) {
   }
   hbmc::plan_warp_kernels(h, d);
   CK(hbmc::setup_warp_kernels());
+  hbmc::plan_tw_kernels(h, d);
+  CK(hbmc::setup_tw_kernels());
+  hbmc::plan_spmv_tma(h, d);
+  CK(hbmc::setup_spmv_tma());
   if (d.sweep_kernel == 2) {
     std::vector<int32_t> rf, rb;
     hbmc::plan_tma(h, d.tma_f, d.tma_b, rf, rb);
@@ -357,8 +361,8 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
   if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown loop mode");
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 2)
-    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be 0, 1 or 2");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 3)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2 or 3");
   if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_tpb must be 0 or a power of two with sweep_tpb * w <= 256");
   hbmc_ctx *ctx = nullptr;

@@ -127,6 +127,21 @@ struct WarpPlan {
   int wpb = 0;
 };
 
+// Shared memory of one warp in the bulk-copy-staged warp-per-unit sweeps
+// (byte offsets: mbarrier at 0, record at 16); ok = false when 4 warps do
+// not fit.
+struct TwPlan {
+  uint32_t off_ts = 0, off_tin = 0, off_ds = 0, off_iv = 0, off_im = 0, warp_bytes = 0;
+  bool ok = false;
+};
+
+// Stage ring of the bulk-copy-fed SpMV (spmv_tma.cu); stages = 0: not used.
+struct SpmvPlan {
+  int64_t nslices = 0, nchunks = 0;
+  uint32_t off_val = 0, off_p = 0, stage_bytes = 0;
+  int stages = 0, blocks_per_sm = 0;
+};
+
 struct TmaPlan {
   int32_t *rec = nullptr;  // device: per level-1 block record
   int rec_ints = 0;
@@ -157,6 +172,8 @@ struct DeviceLayout {
   int32_t *rec_f = nullptr, *rec_b = nullptr, *rec_a = nullptr;
   int64_t max_i_f = 0, max_i_b = 0;
   WarpPlan wp_f64_f, wp_f64_b, wp_f32_f, wp_f32_b, wp_spmv;
+  TwPlan tw_f64_f, tw_f64_b, tw_f32_f, tw_f32_b;
+  SpmvPlan sp;
   int32_t lw = 0;        // log2(w)
   int64_t max_in_f = 0, max_in_b = 0;
   int32_t in_smem_f = 0, in_smem_b = 0;

@@ -527,7 +527,7 @@ int64_t partials_needed(const DeviceLayout &d) {
   int64_t sweep = 0;
   for (int c = 0; c < d.nc; ++c) sweep += (d.tile_ptr[c + 1] - d.tile_ptr[c] + d.sweep_tpb - 1) / d.sweep_tpb;
   const int64_t rows = 2 * (int64_t)row_grid(d);
-  return std::max(std::max(std::max(sweep, rows), tma_partials_needed(d)), warp_partials_needed(d)) + 64;
+  return std::max(std::max(std::max(sweep, rows), tma_partials_needed(d)), std::max(std::max(warp_partials_needed(d), tw_partials_needed(d)), spmv_tma_partials_needed(d))) + 64;
 }
 
 namespace {
@@ -592,6 +592,7 @@ void enqueue_narrow(const double *src, float *dst, int64_t n, cudaStream_t s) {
 }
 
 void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s) {
+  if (spmv_tma_usable(d)) return enqueue_spmv_tma(d, p, q, dot, s);
   if (warp_spmv_usable(d)) return enqueue_spmv_warp(d, p, q, dot, s);
   if (dot)
     k_spmv<true><<<row_grid(d), kRowThreads, 0, s>>>(d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, p, q, d.part, d.sc);
@@ -601,6 +602,7 @@ void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, c
 
 // Forward sweep over all colors: y (F64) or y32 (F32) from r.
 void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
+  if (tw_usable(d, true, prec)) return enqueue_fwd_tw(d, prec, r, check_done, s);
   if (warp_usable(d, true, prec)) return enqueue_fwd_warp(d, prec, r, check_done, s);
   if (tma_usable(d, true, prec)) return enqueue_fwd_tma(d, prec, r, check_done, s);
   const Scalars *sc = check_done ? d.sc : nullptr;
@@ -618,6 +620,7 @@ void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_do
 // Backward sweep over all colors (n_c..1): z from y / y32; dot_mode 0: no
 // dot, 1: initial rho = r.z, 2: rho and beta.
 void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s) {
+  if (tw_usable(d, false, prec)) return enqueue_bwd_tw(d, prec, r, dot_mode, check_done, s);
   if (warp_usable(d, false, prec)) return enqueue_bwd_warp(d, prec, r, dot_mode, check_done, s);
   if (tma_usable(d, false, prec)) return enqueue_bwd_tma(d, prec, r, dot_mode, check_done, s);
   Scalars *sc = check_done || dot_mode ? d.sc : nullptr;

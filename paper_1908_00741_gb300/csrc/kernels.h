@@ -24,6 +24,22 @@ void enqueue_bwd_warp(const DeviceLayout &d, int prec, const double *r, int dot_
                       cudaStream_t s);
 void enqueue_spmv_warp(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);
 
+// Warp-per-unit substitution kernels with bulk-copy staging, bs 4 or 8 (sweep_tw.cu)
+void plan_tw_kernels(const HostLayout &h, DeviceLayout &d);
+cudaError_t setup_tw_kernels();
+bool tw_usable(const DeviceLayout &d, bool fwd, int prec);
+int64_t tw_partials_needed(const DeviceLayout &d);
+void enqueue_fwd_tw(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
+void enqueue_bwd_tw(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                    cudaStream_t s);
+
+// Bulk-copy-fed SpMV, w = 32 (spmv_tma.cu)
+void plan_spmv_tma(const HostLayout &h, DeviceLayout &d);
+cudaError_t setup_spmv_tma();
+bool spmv_tma_usable(const DeviceLayout &d);
+int64_t spmv_tma_partials_needed(const DeviceLayout &d);
+void enqueue_spmv_tma(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);
+
 // TMA-fed substitution kernels (sweep_tma.cu)
 void plan_tma(const HostLayout &h, TmaPlan &pf, TmaPlan &pb, std::vector<int32_t> &rec_f,
               std::vector<int32_t> &rec_b);

@@ -1,0 +1,332 @@
+// Substitution sweeps, one warp per level-1 block with its contiguous
+// operands moved by bulk copy (w = 32, bs = 4 or 8; other shapes use
+// sweep_warp.cu).
+//
+// A warp's work for its level-1 block ("unit", Eq. "BAMC3") is laid out to
+// need few dependent trips to memory:
+//   trip 1  lane 0 starts 1-D bulk copies (cp.async.bulk, completing on a
+//           per-warp mbarrier) of the unit's right-hand-side and dinv
+//           segments -- their addresses follow from the unit index alone --
+//           while every lane loads the unit's record into registers;
+//   trip 2  with the record known, lane 0 adds bulk copies of the unit's
+//           same-block coefficients and their step indices, and the lanes
+//           gather the other-color couplings of Eq. "for3" (coefficient,
+//           column and vector entry, kChunk per lane at a time);
+// then each lane runs its bs-step chain (Eqs. "y2-2", "y2-3") out of shared
+// memory and stores its rows.  Nothing is staged through registers.  The
+// column indices stay out of shared memory on purpose: with them a warp
+// needs about 11 KB (FP64, bs 8) and only 5 CUDA blocks of 4 warps fit on an
+// SM, so the 27 units per SM of a 128^3 color run in two waves; without
+// them 7 blocks fit and one wave covers them.  Per-row term order is the
+// layout's (other colors first, then the same block, farthest column from
+// the diagonal first), identical to the oracle's.
+//
+// With w = 32 every run starts and ends on a multiple of 32 entries and every
+// unit covers 32 * bs consecutive rows, so each copy's addresses and size are
+// multiples of 16 bytes as bulk copies require.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+#include "device_util.cuh"
+#include "hbmc_internal.h"
+#include "kernels.h"
+#include "warp_common.cuh"
+
+namespace hbmc {
+namespace {
+
+constexpr int kTwWarps = 4;
+constexpr int kTwMinBlocks = 7;  // resident CUDA blocks per SM the register budget is cut for
+constexpr uint64_t kTwWaitNs = 4000000000ull;
+constexpr size_t kTwSmemBudget = 200 * 1024;
+constexpr uint32_t kRecOff = 16;  // record after the 8-byte mbarrier; at most 64 ints
+
+template <typename T>
+struct TwArgs {
+  const int32_t *rec;
+  const int32_t *o_col;
+  const T *o_val;
+  const uint8_t *i_m;
+  const T *i_val;
+  const T *dinv;
+  int rec_ints;
+  int64_t tile0, ntiles;
+  uint32_t off_ts, off_tin, off_ds, off_iv, off_im, warp_bytes;
+};
+
+// record int k (k < 64) held by lane k % 32 in r0 (k < 32) or r1
+__device__ __forceinline__ int32_t rec_at(int32_t r0, int32_t r1, int k) {
+  const int32_t a = __shfl_sync(0xffffffffu, r0, k & 31);
+  const int32_t b = __shfl_sync(0xffffffffu, r1, k & 31);
+  return k < 32 ? a : b;
+}
+
+template <int BS, bool FWD, typename T, typename IN, typename G, typename OUT>
+__device__ __forceinline__ void tw_unit(const TwArgs<T> &a, unsigned char *ws, int lane, int64_t u, const IN *in,
+                                        const G *gsrc, OUT *out, const double *r, bool dot, double &rz, Scalars *sc) {
+  constexpr uint32_t R = (uint32_t)BS * 32;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(ws);
+  int32_t *rs = reinterpret_cast<int32_t *>(ws + kRecOff);
+  T *ts = reinterpret_cast<T *>(ws + a.off_ts);
+  IN *tin = reinterpret_cast<IN *>(ws + a.off_tin);  // == ts when IN is T
+  T *ds = reinterpret_cast<T *>(ws + a.off_ds);
+  T *iv = reinterpret_cast<T *>(ws + a.off_iv);
+  uint8_t *im = ws + a.off_im;
+  const int64_t row0 = u * (int64_t)R;
+  // trip 1
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    mbar_expect_tx(bar, R * (uint32_t)(sizeof(IN) + sizeof(T)));
+    tma_load_1d(tin, in + row0, R * (uint32_t)sizeof(IN), bar);
+    tma_load_1d(ds, a.dinv + row0, R * (uint32_t)sizeof(T), bar);
+  }
+  const int32_t *rc = a.rec + u * a.rec_ints;
+  const int32_t r0 = lane < a.rec_ints ? rc[lane] : 0;
+  const int32_t r1 = lane + 32 < a.rec_ints ? rc[lane + 32] : 0;
+  const int olen = rec_at(r0, r1, 0), ilen = rec_at(r0, r1, 1);
+  const int64_t obeg = (int64_t)(((uint64_t)(uint32_t)rec_at(r0, r1, 3) << 32) | (uint32_t)rec_at(r0, r1, 2));
+  const int64_t ibeg = (int64_t)(((uint64_t)(uint32_t)rec_at(r0, r1, 5) << 32) | (uint32_t)rec_at(r0, r1, 4));
+  // trip 2
+  if (lane == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)ilen * (uint32_t)(sizeof(T) + 1));
+    if (ilen > 0) {
+      tma_load_1d(iv, a.i_val + ibeg, (uint32_t)ilen * (uint32_t)sizeof(T), bar);
+      tma_load_1d(im, a.i_m + ibeg, (uint32_t)ilen, bar);
+    }
+  }
+  if (lane < a.rec_ints) rs[lane] = r0;
+  if (lane + 32 < a.rec_ints) rs[lane + 32] = r1;
+  __syncwarp();
+  const uint64_t deadline = global_ns() + kTwWaitNs;
+  const bool ok = mbar_wait(bar, 0, deadline);
+  if (!__all_sync(0xffffffffu, ok)) {
+    if (lane == 0) {
+      sc->timeout = 1;
+      sc->done = 1;
+    }
+    mbar_wait(bar, 0, deadline + kTwWaitNs);  // let the copies land before the warp leaves
+    return;
+  }
+  if constexpr (!std::is_same<IN, T>::value) {
+#pragma unroll
+    for (int l = 0; l < BS; ++l) ts[(l << 5) + lane] = (T)tin[(l << 5) + lane];
+  }
+  // other-color couplings
+  run_accumulate<T, G, true>(a.o_col, a.o_val, gsrc, obeg, olen, rs + 6, ts, lane);
+  const int32_t *i_rel = rs + 7 + BS;
+  double rv[BS];
+  if (!FWD && dot) {
+#pragma unroll
+    for (int q = 0; q < BS; ++q) rv[q] = r[row0 + (q << 5) + lane];
+  }
+  // the bs-step chain: same-block couplings, then the dinv scaling
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    const int lq = FWD ? q : BS - 1 - q;
+    T acc = ts[(lq << 5) + lane];
+    const int pe = i_rel[lq + 1];
+    for (int p = i_rel[lq] + lane; p < pe; p += 32) acc = fma(-iv[p], ts[(im[p] << 5) + lane], acc);
+    ts[(lq << 5) + lane] = acc * ds[(lq << 5) + lane];
+  }
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    const T yv = ts[(q << 5) + lane];
+    out[row0 + (q << 5) + lane] = (OUT)yv;
+    if (!FWD && dot) rz = fma(rv[q], (double)yv, rz);
+  }
+}
+
+template <typename T, typename Y, int BS>
+__global__ void __launch_bounds__(32 * kTwWarps, kTwMinBlocks)
+    k_fwd_tw(const TwArgs<T> a, const double *__restrict__ r, Y *y, Scalars *sc, int check_done) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (check_done && sc->done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = a.tile0 + (int64_t)blockIdx.x * kTwWarps + warp;
+  if (u >= a.tile0 + a.ntiles) return;
+  double rz = 0.0;
+  tw_unit<BS, true, T, double, Y, Y>(a, smem + (size_t)warp * a.warp_bytes, lane, u, r, y, y, nullptr, false, rz, sc);
+}
+
+template <typename T, typename Y, int BS>
+__global__ void __launch_bounds__(32 * kTwWarps, kTwMinBlocks)
+    k_bwd_tw(const TwArgs<T> a, const Y *__restrict__ yin, double *z, const double *__restrict__ r, Scalars *sc,
+             int check_done, int dot_mode, double *part, int64_t part_off, int last_launch, int64_t part_total) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (check_done && sc->done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = a.tile0 + (int64_t)blockIdx.x * kTwWarps + warp;
+  double rz = 0.0;
+  if (u < a.tile0 + a.ntiles)
+    tw_unit<BS, false, T, Y, double, double>(a, smem + (size_t)warp * a.warp_bytes, lane, u, yin, z, z, r,
+                                             dot_mode != 0, rz, sc);
+  if (!dot_mode) return;
+  const double v = block_sum_rt(rz);
+  if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
+  if (!last_launch) return;
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
+  const double rho_new = block_sum_rt(acc);
+  if (threadIdx.x != 0) return;
+  sc->cnt[CNT_RZ] = 0;
+  sc->rho_new = rho_new;
+  if (sc->timeout) return;
+  if (!(rho_new > 0.0) || !finite(rho_new)) {
+    sc->status = ST_BREAKDOWN;
+    sc->done = 1;
+    return;
+  }
+  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
+  sc->rho = rho_new;
+}
+
+uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
+
+template <typename T>
+TwArgs<T> tw_args(const DeviceLayout &d, bool fwd, int c, const TwPlan &p) {
+  TwArgs<T> a;
+  a.rec = fwd ? d.rec_f : d.rec_b;
+  a.rec_ints = d.rec_ints;
+  a.o_col = fwd ? d.fo_col : d.bo_col;
+  a.i_m = fwd ? d.fi_m : d.bi_m;
+  if constexpr (sizeof(T) == 8) {
+    a.o_val = (const T *)(fwd ? d.fo_val : d.bo_val);
+    a.i_val = (const T *)(fwd ? d.fi_val : d.bi_val);
+    a.dinv = (const T *)d.dinv;
+  } else {
+    a.o_val = (const T *)(fwd ? d.fo_val32 : d.bo_val32);
+    a.i_val = (const T *)(fwd ? d.fi_val32 : d.bi_val32);
+    a.dinv = (const T *)d.dinv32;
+  }
+  a.tile0 = d.tile_ptr[c];
+  a.ntiles = d.tile_ptr[c + 1] - d.tile_ptr[c];
+  a.off_ts = p.off_ts;
+  a.off_tin = p.off_tin;
+  a.off_ds = p.off_ds;
+  a.off_iv = p.off_iv;
+  a.off_im = p.off_im;
+  a.warp_bytes = p.warp_bytes;
+  return a;
+}
+
+// Forward sweeps read the double right-hand side r; in FP32 it lands in a
+// region of its own and is narrowed into ts.  Every other case copies the
+// input straight into ts.
+TwPlan plan_one(int bs, bool fwd, int rec_ints, int64_t max_i, size_t tsize) {
+  TwPlan p;
+  const uint64_t R = (uint64_t)bs * 32;
+  p.off_ts = a16(kRecOff + 4ull * 64);
+  uint64_t next = p.off_ts + R * tsize;
+  p.off_tin = p.off_ts;
+  if (fwd && tsize != 8) {
+    p.off_tin = a16(next);
+    next = p.off_tin + R * 8;
+  }
+  p.off_ds = a16(next);
+  p.off_iv = a16(p.off_ds + R * tsize);
+  p.off_im = a16(p.off_iv + (uint64_t)max_i * tsize);
+  p.warp_bytes = (uint32_t)((p.off_im + (uint64_t)max_i + 127) & ~uint64_t(127));
+  p.ok = rec_ints <= 64 && (uint64_t)kTwWarps * p.warp_bytes <= kTwSmemBudget;
+  return p;
+}
+
+const TwPlan &tw_plan(const DeviceLayout &d, bool fwd, int prec) {
+  return prec == HBMC_PREC_F64 ? (fwd ? d.tw_f64_f : d.tw_f64_b) : (fwd ? d.tw_f32_f : d.tw_f32_b);
+}
+
+unsigned tw_grid(const DeviceLayout &d, int c) {
+  return (unsigned)((d.tile_ptr[c + 1] - d.tile_ptr[c] + kTwWarps - 1) / kTwWarps);
+}
+
+template <typename T, typename Y, int BS>
+void launch_fwd(const DeviceLayout &d, const double *r, Y *y, bool check_done, cudaStream_t s, const TwPlan &p) {
+  for (int c = 0; c < d.nc; ++c)
+    k_fwd_tw<T, Y, BS><<<tw_grid(d, c), 32 * kTwWarps, (size_t)kTwWarps * p.warp_bytes, s>>>(
+        tw_args<T>(d, true, c, p), r, y, d.sc, check_done ? 1 : 0);
+}
+
+template <typename T, typename Y, int BS>
+void launch_bwd(const DeviceLayout &d, const Y *yin, const double *r, int dot_mode, bool check_done, cudaStream_t s,
+                const TwPlan &p) {
+  int64_t total = 0;
+  for (int c = 0; c < d.nc; ++c) total += tw_grid(d, c);
+  int64_t off = 0;
+  for (int c = d.nc - 1; c >= 0; --c) {
+    const unsigned grid = tw_grid(d, c);
+    k_bwd_tw<T, Y, BS><<<grid, 32 * kTwWarps, (size_t)kTwWarps * p.warp_bytes, s>>>(
+        tw_args<T>(d, false, c, p), yin, d.z, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, off, c == 0 ? 1 : 0,
+        total);
+    off += grid;
+  }
+}
+
+template <typename K>
+cudaError_t allow(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTwSmemBudget);
+}
+
+}  // namespace
+
+void plan_tw_kernels(const HostLayout &h, DeviceLayout &d) {
+  d.tw_f64_f = plan_one(h.bs, true, h.rec_ints, h.max_i_f, 8);
+  d.tw_f64_b = plan_one(h.bs, false, h.rec_ints, h.max_i_b, 8);
+  d.tw_f32_f = plan_one(h.bs, true, h.rec_ints, h.max_i_f, 4);
+  d.tw_f32_b = plan_one(h.bs, false, h.rec_ints, h.max_i_b, 4);
+}
+
+cudaError_t setup_tw_kernels() {
+  cudaError_t e;
+  if ((e = allow(k_fwd_tw<double, double, 4>)) || (e = allow(k_fwd_tw<double, double, 8>)) ||
+      (e = allow(k_fwd_tw<float, float, 4>)) || (e = allow(k_fwd_tw<float, float, 8>)) ||
+      (e = allow(k_bwd_tw<double, double, 4>)) || (e = allow(k_bwd_tw<double, double, 8>)) ||
+      (e = allow(k_bwd_tw<float, float, 4>)) || (e = allow(k_bwd_tw<float, float, 8>)))
+    return e;
+  return cudaSuccess;
+}
+
+bool tw_usable(const DeviceLayout &d, bool fwd, int prec) {
+  return d.sweep_kernel == 0 && d.w == 32 && (d.bs == 4 || d.bs == 8) && d.rec_f && tw_plan(d, fwd, prec).ok;
+}
+
+int64_t tw_partials_needed(const DeviceLayout &d) {
+  int64_t t = 0;
+  for (int c = 0; c < d.nc; ++c) t += tw_grid(d, c);
+  return t;
+}
+
+void enqueue_fwd_tw(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
+  const TwPlan &p = tw_plan(d, true, prec);
+  if (prec == HBMC_PREC_F64) {
+    if (d.bs == 4) launch_fwd<double, double, 4>(d, r, d.y, check_done, s, p);
+    else launch_fwd<double, double, 8>(d, r, d.y, check_done, s, p);
+  } else {
+    if (d.bs == 4) launch_fwd<float, float, 4>(d, r, d.y32, check_done, s, p);
+    else launch_fwd<float, float, 8>(d, r, d.y32, check_done, s, p);
+  }
+}
+
+void enqueue_bwd_tw(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s) {
+  const TwPlan &p = tw_plan(d, false, prec);
+  if (prec == HBMC_PREC_F64) {
+    if (d.bs == 4) launch_bwd<double, double, 4>(d, d.y, r, dot_mode, check_done, s, p);
+    else launch_bwd<double, double, 8>(d, d.y, r, dot_mode, check_done, s, p);
+  } else {
+    if (d.bs == 4) launch_bwd<float, float, 4>(d, d.y32, r, dot_mode, check_done, s, p);
+    else launch_bwd<float, float, 8>(d, d.y32, r, dot_mode, check_done, s, p);
+  }
+}
+
+}  // namespace hbmc

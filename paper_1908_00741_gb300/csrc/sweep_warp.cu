@@ -292,10 +292,10 @@ cudaError_t setup_warp_kernels() {
 }
 
 bool warp_usable(const DeviceLayout &d, bool fwd, int prec) {
-  return d.sweep_kernel == 0 && d.w == 32 && d.rec_f && plan_of(d, fwd, prec).wpb > 0;
+  return (d.sweep_kernel == 0 || d.sweep_kernel == 3) && d.w == 32 && d.rec_f && plan_of(d, fwd, prec).wpb > 0;
 }
 
-bool warp_spmv_usable(const DeviceLayout &d) { return d.w == 32 && d.rec_a && d.wp_spmv.wpb > 0; }
+bool warp_spmv_usable(const DeviceLayout &d) { return d.sweep_kernel == 3 && d.w == 32 && d.rec_a && d.wp_spmv.wpb > 0; }
 
 int64_t warp_partials_needed(const DeviceLayout &d) {
   int64_t need = 0;

@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 CASES = [
     ("poisson7_8_bs8_w32", lambda: W.poisson7(8), 8, 32, (2, 2, 2)),
     ("poisson7_7_ragged", lambda: W.poisson7(7), 8, 32, (2, 2, 2)),
+    ("poisson7_9_bs4_w32", lambda: W.poisson7(9), 4, 32, (1, 2, 2)),
     ("poisson7_10_bs16_w8", lambda: W.poisson7(10), 16, 8, (2, 2, 4)),
     ("poisson7_9_bs32_w4", lambda: W.poisson7(9), 32, 4, (2, 4, 4)),
     ("hetero27_9_rand", lambda: W.permute_input(W.heterogeneous_stencil(9, 27, 2.0, 1),
@@ -346,12 +347,13 @@ def test_sweep_geometry_variants_bitwise(lib, orc, tpb, w, bs):
 @pytest.mark.parametrize("name,mk,bs,w,box", [c for c in CASES if c[3] == 32])
 @pytest.mark.parametrize("precision", [H.PREC_F64, H.PREC_F32])
 def test_sweep_kernel_variants_agree(lib, orc, name, mk, bs, w, box, precision):
-    """The warp-per-unit kernels (default for w = 32), the block-per-unit
-    kernels and the TMA-fed kernels compute the same bits, in both
-    precisions, and FP64 matches the oracle."""
+    """The warp-per-unit kernels (default for w = 32; runs staged by bulk
+    copy for bs 4 and 8, plain loads with sweep_kernel 3), the
+    block-per-unit kernels and the TMA-fed kernels compute the same bits, in
+    both precisions, and FP64 matches the oracle."""
     A = mk()
     outs = []
-    for sk in (0, 1, 2):
+    for sk in (0, 1, 2, 3):
         ctx = H.hbmc_build(A, bs, w, box=box, sweep_kernel=sk, precision=precision)
         assert H.hbmc_ic0(ctx, 0.1)[0] == H.OK
         n_pad = ctx.info()["n_pad"]
