@@ -267,13 +267,15 @@ def test_not_spd_pivot_reports_oracle_row(lib, orc):
             H.hbmc_iccg(ctx, dev(np.ones(A.n)), torch.zeros(A.n, dtype=torch.float64, device="cuda"))
 
 
-def test_cg_breakdown_matches_oracle(lib, orc):
+@pytest.mark.parametrize("bs,w", [(4, 2), (4, 32), (8, 32)])
+def test_cg_breakdown_matches_oracle(lib, orc, bs, w):
     """Indefinite A with a shift large enough for IC(0): CG breaks down on a
-    non-positive p.q, at the same iteration as the oracle."""
+    non-positive p.q, at the same iteration as the oracle, for the plain
+    and the bulk-copy-fed kernels."""
     A = _indefinite()
-    ctx = H.hbmc_build(A, 4, 2)
+    ctx = H.hbmc_build(A, bs, w)
     assert H.hbmc_ic0(ctx, 2.0)[0] == H.OK
-    an = orc.analyse(A, 4, 2)
+    an = orc.analyse(A, bs, w)
     lval, _, dinv, _ = orc.factor(an, 2.0)
     b = np.cos(np.arange(A.n))
     ref = orc.pcg(an, lval, dinv, b, tol=1e-12, maxit=500)
