@@ -130,16 +130,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_traffic(kernel, source):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture
-    (profiles/traffic.json), or None when the kernel source changed since."""
+TRAFFIC_RECORD = os.path.join("profiles", "spmv_tma_poisson128_bs8_f64.md")
+SPMV_SOURCE = os.path.join("paper_1908_00741_gb300", "csrc", "spmv_tma.cu")
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the SpMV kernel from the committed ncu summary
+    (its `traffic:` line), or None when the kernel source changed since the
+    counters were taken (the line carries the source's sha1)."""
     import hashlib
+    import re
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "spmv_poisson128_bs8_dram.json")))[kernel]
-        sha = hashlib.sha1(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
-        return rec["bytes_per_launch"] if rec.get("source_sha1") == sha else None
+        text = open(os.path.join(ROOT, TRAFFIC_RECORD)).read()
+        m = re.search(r"traffic: kernel=(\S+) bytes_per_launch=(\d+) source=(\S+) sha1=([0-9a-f]+)", text)
+        sha = hashlib.sha1(open(os.path.join(ROOT, m.group(3)), "rb").read()).hexdigest()
+        return int(m.group(2)) if sha == m.group(4) else None
     except Exception:
         return None
+
+
+# Nominal FP64 rate of a GB300 (1.25 TFLOP/s dense): the ceiling for the
+# FP64 fused multiply-adds every kernel of the FP64 path issues.
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 def subst_bytes(n, nnz_lower, s):
@@ -269,10 +281,15 @@ def run_gpu(args):
     gbs["update_p"] = 3 * A.n * 8 / (kernel_ms["update_p"] * 1e-3) / 1e9
 
     # dominant kernel of a solve: SpMV (the largest share in the launch list)
-    traffic = measured_traffic("spmv", "paper_1908_00741_gb300/csrc/sweep_warp.cu")
-    roofline = {"bound": "hbm", "kernel": "spmv (q = A p, fused p.q)", "achieved": round(gbs["spmv"], 1),
+    traffic = measured_traffic()
+    sp_fma = A.nnz + A.n  # q = A p plus the fused p.q
+    sp_tflops = 2 * sp_fma / (kernel_ms["spmv"] * 1e-3) / 1e12
+    roofline = {"bound": "hbm", "kernel": "k_spmv_tma (q = A p, fused p.q)", "achieved": round(gbs["spmv"], 1),
                 "peak": peak, "unit": "GB/s", "frac": round(gbs["spmv"] / peak, 4),
-                "traffic": traffic, "algorithmic_bytes": sp_bytes, "peak_source": peak_kind}
+                "traffic": traffic, "algorithmic_bytes": sp_bytes, "peak_source": peak_kind,
+                "fp64": {"fma_per_launch": sp_fma, "achieved_tflops": round(sp_tflops, 4),
+                         "peak_tflops": FP64_NOMINAL_TFLOPS, "frac": round(sp_tflops / FP64_NOMINAL_TFLOPS, 4),
+                         "peak_source": "nominal"}}
     subst = {k: {"GB/s": round(v, 1), "frac": round(v / peak, 4), "ms": round(kernel_ms[k], 4)}
              for k, v in gbs.items()}
 
