@@ -86,8 +86,15 @@ typedef struct hbmc_options {
                            1 = one CUDA block per level-1 block(s);
                            2 = TMA-fed persistent warp-specialized kernels (w = 32);
                            3 = one warp per level-1 block reading its runs with plain loads,
-                               and SpMV one warp per level-1 block too (w = 32).
-                           SpMV runs one thread per row except with 3. */
+                               and SpMV one warp per level-1 block too (w = 32);
+                           4 = one CUDA block of loader threads per level-1 block for every
+                               color (automatic under 0, when bs is 4 or 8 and w = 32, for
+                               colors whose level-1 blocks average 2048 or more other-color
+                               couplings or that have fewer level-1 blocks than SMs);
+                           5 = the bulk-copy-staged warp kernels of 0 for every color. 
+                           SpMV (w = 32) is fed by bulk copies when a chunk of its slices fits
+                           in shared memory, else one thread per row; with 3 it runs one warp
+                           per level-1 block. */
 } hbmc_options;
 
 /* Fills *opt with the defaults. */

@@ -152,6 +152,7 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dalloc(ctx, d.y, nv));
   TRY(dalloc(ctx, d.t, nv));
   TRY(dalloc(ctx, d.y32, nv));
+  TRY(dalloc(ctx, d.z32, nv));
   CK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
   while ((1 << d.lw) < d.w) ++d.lw;
   hbmc::sweep_geometry(h, d, ctx->opt.sweep_tpb);
@@ -168,6 +169,8 @@ hbmc_status upload(hbmc_ctx *ctx) {
   CK(hbmc::setup_tw_kernels());
   hbmc::plan_spmv_tma(h, d);
   CK(hbmc::setup_spmv_tma());
+  hbmc::plan_wide_kernels(h, d);
+  CK(hbmc::setup_wide_kernels());
   if (d.sweep_kernel == 2) {
     std::vector<int32_t> rf, rb;
     hbmc::plan_tma(h, d.tma_f, d.tma_b, rf, rb);
@@ -361,8 +364,8 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
   if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown loop mode");
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 3)
-    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2 or 3");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 5)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..5");
   if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_tpb must be 0 or a power of two with sweep_tpb * w <= 256");
   hbmc_ctx *ctx = nullptr;

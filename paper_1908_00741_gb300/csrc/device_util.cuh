@@ -61,6 +61,15 @@ __device__ double gather_partials(const double *part, int64_t count, int stride,
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
+// Backward sweeps in FP32 gather z from its FP32 copy z32: z holds those
+// FP32 results widened, so the narrowed gather gives the same value at half
+// the bytes and without an FP64-pipe conversion.  FP64 sweeps gather z.
+template <typename T>
+__device__ __forceinline__ const T *zgather(const double *z, const float *z32) {
+  if constexpr (sizeof(T) == 4) return reinterpret_cast<const T *>(z32);
+  else return reinterpret_cast<const T *>(z);
+}
+
 // Row kernels run a fixed grid (a few CUDA blocks per SM) and loop over the
 // rows with a grid stride, so each thread accumulates its dot-product terms
 // over several rows before the block reduction.

@@ -135,6 +135,13 @@ struct TwPlan {
   bool ok = false;
 };
 
+// Shared memory of the loader-thread sweeps (sweep_wide.cu), byte offsets;
+// ok = false when a level-1 block's runs do not fit.
+struct WidePlan {
+  uint32_t off_ts = 0, off_ds = 0, off_rr = 0, off_vv = 0, off_gv = 0, off_iv = 0, off_im = 0, smem_bytes = 0;
+  bool ok = false;
+};
+
 // Stage ring of the bulk-copy-fed SpMV (spmv_tma.cu); stages = 0: not used.
 struct SpmvPlan {
   int64_t nslices = 0, nchunks = 0;
@@ -174,6 +181,8 @@ struct DeviceLayout {
   WarpPlan wp_f64_f, wp_f64_b, wp_f32_f, wp_f32_b, wp_spmv;
   TwPlan tw_f64_f, tw_f64_b, tw_f32_f, tw_f32_b;
   SpmvPlan sp;
+  WidePlan wd_f64_f, wd_f64_b, wd_f32_f, wd_f32_b;
+  std::vector<uint8_t> wide_f, wide_b;  // per color: the loader-thread sweep is the faster one
   int32_t lw = 0;        // log2(w)
   int64_t max_in_f = 0, max_in_b = 0;
   int32_t in_smem_f = 0, in_smem_b = 0;
@@ -196,7 +205,7 @@ struct DeviceLayout {
   // vectors in HBMC order, n_pad + kGuard doubles (guard entries stay 0)
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
          *y = nullptr, *t = nullptr;
-  float *y32 = nullptr;
+  float *y32 = nullptr, *z32 = nullptr;
   double *part = nullptr;  // reduction partials
   int64_t part_len = 0;
   double *hist = nullptr;

@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kTileThreads)
 // of the last color (color 1) finishes the sum over every color's partials.
 template <typename T, typename Y>
 __global__ void __launch_bounds__(kTileThreads)
-    k_bwd(const SweepArgs<T> a, const Y *__restrict__ yin, double *z, const double *__restrict__ r,
+    k_bwd(const SweepArgs<T> a, const Y *__restrict__ yin, double *z, float *z32, const double *__restrict__ r,
           Scalars *sc, int dot_mode, double *part, int64_t part_off, int last_launch,
           int64_t part_total) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -349,7 +349,8 @@ __global__ void __launch_bounds__(kTileThreads)
     const int j = (int)(row & (a.w - 1));
     T acc = (T)yin[row];
     const int64_t pe = a.o_ptr[s + 1];
-    for (int64_t p = a.o_ptr[s] + j; p < pe; p += a.w) acc = fma(-a.o_val[p], (T)z[a.o_col[p]], acc);
+    const T *zg = zgather<T>(z, z32);
+    for (int64_t p = a.o_ptr[s] + j; p < pe; p += a.w) acc = fma(-a.o_val[p], zg[a.o_col[p]], acc);
     m.tv[lr] = acc;
     m.dv[lr] = a.dinv[row];
   }
@@ -375,6 +376,7 @@ __global__ void __launch_bounds__(kTileThreads)
   for (int lr = threadIdx.x; lr < nrows; lr += kTileThreads) {
     const double zv = (double)m.tv[lr];
     z[row0 + lr] = zv;
+    if constexpr (sizeof(T) == 4) z32[row0 + lr] = m.tv[lr];
     if (dot_mode) rz = fma(r[row0 + lr], zv, rz);
   }
   if (!dot_mode) return;
@@ -527,7 +529,7 @@ int64_t partials_needed(const DeviceLayout &d) {
   int64_t sweep = 0;
   for (int c = 0; c < d.nc; ++c) sweep += (d.tile_ptr[c + 1] - d.tile_ptr[c] + d.sweep_tpb - 1) / d.sweep_tpb;
   const int64_t rows = 2 * (int64_t)row_grid(d);
-  return std::max(std::max(std::max(sweep, rows), tma_partials_needed(d)), std::max(std::max(warp_partials_needed(d), tw_partials_needed(d)), spmv_tma_partials_needed(d))) + 64;
+  return std::max(std::max(std::max(sweep, rows), tma_partials_needed(d)), std::max(std::max(warp_partials_needed(d), tw_partials_needed(d)), std::max(spmv_tma_partials_needed(d), d.nc > 0 ? d.tile_ptr[d.nc] : (int64_t)0))) + 64;
 }
 
 namespace {
@@ -601,8 +603,18 @@ void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, c
 }
 
 // Forward sweep over all colors: y (F64) or y32 (F32) from r.
+// Colors pick their kernel one by one: the loader-thread kernel for colors
+// with long other-color runs or few level-1 blocks, else the
+// bulk-copy-staged warp kernel; both give the same bits.
 void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
-  if (tw_usable(d, true, prec)) return enqueue_fwd_tw(d, prec, r, check_done, s);
+  const bool wide = wide_usable(d, true, prec), tw = tw_usable(d, true, prec);
+  if ((wide && d.sweep_kernel == 4) || tw) {
+    for (int c = 0; c < d.nc; ++c) {
+      if (wide && wide_preferred(d, true, c)) launch_fwd_wide_color(d, prec, c, r, check_done, s);
+      else launch_fwd_tw_color(d, prec, c, r, check_done, s);
+    }
+    return;
+  }
   if (warp_usable(d, true, prec)) return enqueue_fwd_warp(d, prec, r, check_done, s);
   if (tma_usable(d, true, prec)) return enqueue_fwd_tma(d, prec, r, check_done, s);
   const Scalars *sc = check_done ? d.sc : nullptr;
@@ -620,7 +632,23 @@ void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_do
 // Backward sweep over all colors (n_c..1): z from y / y32; dot_mode 0: no
 // dot, 1: initial rho = r.z, 2: rho and beta.
 void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s) {
-  if (tw_usable(d, false, prec)) return enqueue_bwd_tw(d, prec, r, dot_mode, check_done, s);
+  const bool wide = wide_usable(d, false, prec), tw = tw_usable(d, false, prec);
+  if ((wide && d.sweep_kernel == 4) || tw) {
+    auto use_wide = [&](int c) { return wide && wide_preferred(d, false, c); };
+    int64_t total = 0;
+    for (int c = 0; c < d.nc; ++c) total += use_wide(c) ? wide_color_grid(d, c) : tw_color_grid(d, c);
+    int64_t off = 0;
+    for (int c = d.nc - 1; c >= 0; --c) {
+      if (use_wide(c)) {
+        launch_bwd_wide_color(d, prec, c, r, dot_mode, check_done, off, c == 0, total, s);
+        off += wide_color_grid(d, c);
+      } else {
+        launch_bwd_tw_color(d, prec, c, r, dot_mode, check_done, off, c == 0, total, s);
+        off += tw_color_grid(d, c);
+      }
+    }
+    return;
+  }
   if (warp_usable(d, false, prec)) return enqueue_bwd_warp(d, prec, r, dot_mode, check_done, s);
   if (tma_usable(d, false, prec)) return enqueue_bwd_tma(d, prec, r, dot_mode, check_done, s);
   Scalars *sc = check_done || dot_mode ? d.sc : nullptr;
@@ -632,10 +660,10 @@ void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode,
     const int last = c == 0;
     if (prec == HBMC_PREC_F64) {
       const SweepArgs<double> a = sweep_args<double>(d, false, c);
-      k_bwd<double, double><<<grid, kTileThreads, sweep_smem(a), s>>>(a, d.y, d.z, r, sc, dot_mode, d.part, off, last, total);
+      k_bwd<double, double><<<grid, kTileThreads, sweep_smem(a), s>>>(a, d.y, d.z, d.z32, r, sc, dot_mode, d.part, off, last, total);
     } else {
       const SweepArgs<float> a = sweep_args<float>(d, false, c);
-      k_bwd<float, float><<<grid, kTileThreads, sweep_smem(a), s>>>(a, d.y32, d.z, r, sc, dot_mode, d.part, off, last, total);
+      k_bwd<float, float><<<grid, kTileThreads, sweep_smem(a), s>>>(a, d.y32, d.z, d.z32, r, sc, dot_mode, d.part, off, last, total);
     }
     off += grid;
   }

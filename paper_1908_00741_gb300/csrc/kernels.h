@@ -29,9 +29,21 @@ void plan_tw_kernels(const HostLayout &h, DeviceLayout &d);
 cudaError_t setup_tw_kernels();
 bool tw_usable(const DeviceLayout &d, bool fwd, int prec);
 int64_t tw_partials_needed(const DeviceLayout &d);
-void enqueue_fwd_tw(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
-void enqueue_bwd_tw(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
-                    cudaStream_t s);
+unsigned tw_color_grid(const DeviceLayout &d, int c);
+void launch_fwd_tw_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done, cudaStream_t s);
+void launch_bwd_tw_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
+                         int64_t part_off, bool last, int64_t part_total, cudaStream_t s);
+
+// One CUDA block per level-1 block with loader threads (sweep_wide.cu): for
+// colors with few level-1 blocks, where one warp per block leaves the GPU idle
+void plan_wide_kernels(const HostLayout &h, DeviceLayout &d);
+cudaError_t setup_wide_kernels();
+bool wide_usable(const DeviceLayout &d, bool fwd, int prec);
+bool wide_preferred(const DeviceLayout &d, bool fwd, int c);
+unsigned wide_color_grid(const DeviceLayout &d, int c);
+void launch_fwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done, cudaStream_t s);
+void launch_bwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
+                           int64_t part_off, bool last, int64_t part_total, cudaStream_t s);
 
 // Bulk-copy-fed SpMV, w = 32 (spmv_tma.cu)
 void plan_spmv_tma(const HostLayout &h, DeviceLayout &d);

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
 // beta; the launch of color 1 (last_launch) finishes the sum.
 template <typename T, typename Y>
 __global__ void __launch_bounds__(kTmaThreads, 3)
-    k_bwd_tma(const TmaSweep<T> a, const Y *__restrict__ yin, double *z, const double *__restrict__ r,
+    k_bwd_tma(const TmaSweep<T> a, const Y *__restrict__ yin, double *z, float *z32, const double *__restrict__ r,
               Scalars *sc, int check_done, int dot_mode, double *part, int64_t part_off,
               int last_launch, int64_t part_total) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
           const int l = lr >> 5, j = lr & 31;
           T acc = (T)yseg[lr];
           const int pe = o_rel[l + 1];
-          for (int p = o_rel[l] + j; p < pe; p += 32) acc = fma(-oval[p], (T)z[ocol[p]], acc);
+          const T *zg = zgather<T>(z, z32);
+          for (int p = o_rel[l] + j; p < pe; p += 32) acc = fma(-oval[p], zg[ocol[p]], acc);
           tv[lr] = acc;
         }
       }
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
         for (int lr = ct; lr < R; lr += kConsThreads) {
           const double zv = (double)tv[lr];
           zo[lr] = zv;
+          if constexpr (sizeof(T) == 4) z32[u * R + lr] = tv[lr];
           if (dot_mode) rz = fma(rseg[lr], zv, rz);
         }
       }
@@ -458,11 +460,11 @@ void enqueue_bwd_tma(const DeviceLayout &d, int prec, const double *r, int dot_m
     if (prec == HBMC_PREC_F64) {
       const TmaSweep<double> a = tma_args<double>(d, false, c);
       k_bwd_tma<double, double><<<grid, kTmaThreads, tma_smem(d, L, 8), s>>>(
-          a, d.y, d.z, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, off, last, total);
+          a, d.y, d.z, d.z32, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, off, last, total);
     } else {
       const TmaSweep<float> a = tma_args<float>(d, false, c);
       k_bwd_tma<float, float><<<grid, kTmaThreads, tma_smem(d, L, 4), s>>>(
-          a, d.y32, d.z, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, off, last, total);
+          a, d.y32, d.z, d.z32, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, off, last, total);
     }
     off += grid;
   }

@@ -66,7 +66,8 @@ __device__ __forceinline__ int32_t rec_at(int32_t r0, int32_t r1, int k) {
 
 template <int BS, bool FWD, typename T, typename IN, typename G, typename OUT>
 __device__ __forceinline__ void tw_unit(const TwArgs<T> &a, unsigned char *ws, int lane, int64_t u, const IN *in,
-                                        const G *gsrc, OUT *out, const double *r, bool dot, double &rz, Scalars *sc) {
+                                        const G *gsrc, OUT *out, const double *r, bool dot, double &rz, Scalars *sc,
+                                        float *out32 = nullptr) {
   constexpr uint32_t R = (uint32_t)BS * 32;
   uint64_t *bar = reinterpret_cast<uint64_t *>(ws);
   int32_t *rs = reinterpret_cast<int32_t *>(ws + kRecOff);
@@ -136,6 +137,7 @@ __device__ __forceinline__ void tw_unit(const TwArgs<T> &a, unsigned char *ws, i
   for (int q = 0; q < BS; ++q) {
     const T yv = ts[(q << 5) + lane];
     out[row0 + (q << 5) + lane] = (OUT)yv;
+    if constexpr (!FWD && sizeof(T) == 4) out32[row0 + (q << 5) + lane] = yv;
     if (!FWD && dot) rz = fma(rv[q], (double)yv, rz);
   }
 }
@@ -154,16 +156,17 @@ __global__ void __launch_bounds__(32 * kTwWarps, kTwMinBlocks)
 
 template <typename T, typename Y, int BS>
 __global__ void __launch_bounds__(32 * kTwWarps, kTwMinBlocks)
-    k_bwd_tw(const TwArgs<T> a, const Y *__restrict__ yin, double *z, const double *__restrict__ r, Scalars *sc,
-             int check_done, int dot_mode, double *part, int64_t part_off, int last_launch, int64_t part_total) {
+    k_bwd_tw(const TwArgs<T> a, const Y *__restrict__ yin, double *z, float *z32, const double *__restrict__ r,
+             Scalars *sc, int check_done, int dot_mode, double *part, int64_t part_off, int last_launch,
+             int64_t part_total) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (check_done && sc->done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t u = a.tile0 + (int64_t)blockIdx.x * kTwWarps + warp;
   double rz = 0.0;
   if (u < a.tile0 + a.ntiles)
-    tw_unit<BS, false, T, Y, double, double>(a, smem + (size_t)warp * a.warp_bytes, lane, u, yin, z, z, r,
-                                             dot_mode != 0, rz, sc);
+    tw_unit<BS, false, T, Y, T, double>(a, smem + (size_t)warp * a.warp_bytes, lane, u, yin, zgather<T>(z, z32), z,
+                                        r, dot_mode != 0, rz, sc, z32);
   if (!dot_mode) return;
   const double v = block_sum_rt(rz);
   if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
@@ -252,25 +255,18 @@ unsigned tw_grid(const DeviceLayout &d, int c) {
 }
 
 template <typename T, typename Y, int BS>
-void launch_fwd(const DeviceLayout &d, const double *r, Y *y, bool check_done, cudaStream_t s, const TwPlan &p) {
-  for (int c = 0; c < d.nc; ++c)
-    k_fwd_tw<T, Y, BS><<<tw_grid(d, c), 32 * kTwWarps, (size_t)kTwWarps * p.warp_bytes, s>>>(
-        tw_args<T>(d, true, c, p), r, y, d.sc, check_done ? 1 : 0);
+void launch_fwd(const DeviceLayout &d, int c, const double *r, Y *y, bool check_done, cudaStream_t s,
+                const TwPlan &p) {
+  k_fwd_tw<T, Y, BS><<<tw_grid(d, c), 32 * kTwWarps, (size_t)kTwWarps * p.warp_bytes, s>>>(
+      tw_args<T>(d, true, c, p), r, y, d.sc, check_done ? 1 : 0);
 }
 
 template <typename T, typename Y, int BS>
-void launch_bwd(const DeviceLayout &d, const Y *yin, const double *r, int dot_mode, bool check_done, cudaStream_t s,
-                const TwPlan &p) {
-  int64_t total = 0;
-  for (int c = 0; c < d.nc; ++c) total += tw_grid(d, c);
-  int64_t off = 0;
-  for (int c = d.nc - 1; c >= 0; --c) {
-    const unsigned grid = tw_grid(d, c);
-    k_bwd_tw<T, Y, BS><<<grid, 32 * kTwWarps, (size_t)kTwWarps * p.warp_bytes, s>>>(
-        tw_args<T>(d, false, c, p), yin, d.z, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, off, c == 0 ? 1 : 0,
-        total);
-    off += grid;
-  }
+void launch_bwd(const DeviceLayout &d, int c, const Y *yin, const double *r, int dot_mode, bool check_done,
+                int64_t part_off, bool last, int64_t part_total, cudaStream_t s, const TwPlan &p) {
+  k_bwd_tw<T, Y, BS><<<tw_grid(d, c), 32 * kTwWarps, (size_t)kTwWarps * p.warp_bytes, s>>>(
+      tw_args<T>(d, false, c, p), yin, d.z, d.z32, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, part_off,
+      last ? 1 : 0, part_total);
 }
 
 template <typename K>
@@ -298,7 +294,8 @@ cudaError_t setup_tw_kernels() {
 }
 
 bool tw_usable(const DeviceLayout &d, bool fwd, int prec) {
-  return d.sweep_kernel == 0 && d.w == 32 && (d.bs == 4 || d.bs == 8) && d.rec_f && tw_plan(d, fwd, prec).ok;
+  return (d.sweep_kernel == 0 || d.sweep_kernel == 5) && d.w == 32 && (d.bs == 4 || d.bs == 8) && d.rec_f &&
+         tw_plan(d, fwd, prec).ok;
 }
 
 int64_t tw_partials_needed(const DeviceLayout &d) {
@@ -307,25 +304,28 @@ int64_t tw_partials_needed(const DeviceLayout &d) {
   return t;
 }
 
-void enqueue_fwd_tw(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
+unsigned tw_color_grid(const DeviceLayout &d, int c) { return tw_grid(d, c); }
+
+void launch_fwd_tw_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done, cudaStream_t s) {
   const TwPlan &p = tw_plan(d, true, prec);
   if (prec == HBMC_PREC_F64) {
-    if (d.bs == 4) launch_fwd<double, double, 4>(d, r, d.y, check_done, s, p);
-    else launch_fwd<double, double, 8>(d, r, d.y, check_done, s, p);
+    if (d.bs == 4) launch_fwd<double, double, 4>(d, c, r, d.y, check_done, s, p);
+    else launch_fwd<double, double, 8>(d, c, r, d.y, check_done, s, p);
   } else {
-    if (d.bs == 4) launch_fwd<float, float, 4>(d, r, d.y32, check_done, s, p);
-    else launch_fwd<float, float, 8>(d, r, d.y32, check_done, s, p);
+    if (d.bs == 4) launch_fwd<float, float, 4>(d, c, r, d.y32, check_done, s, p);
+    else launch_fwd<float, float, 8>(d, c, r, d.y32, check_done, s, p);
   }
 }
 
-void enqueue_bwd_tw(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s) {
+void launch_bwd_tw_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
+                         int64_t part_off, bool last, int64_t part_total, cudaStream_t s) {
   const TwPlan &p = tw_plan(d, false, prec);
   if (prec == HBMC_PREC_F64) {
-    if (d.bs == 4) launch_bwd<double, double, 4>(d, d.y, r, dot_mode, check_done, s, p);
-    else launch_bwd<double, double, 8>(d, d.y, r, dot_mode, check_done, s, p);
+    if (d.bs == 4) launch_bwd<double, double, 4>(d, c, d.y, r, dot_mode, check_done, part_off, last, part_total, s, p);
+    else launch_bwd<double, double, 8>(d, c, d.y, r, dot_mode, check_done, part_off, last, part_total, s, p);
   } else {
-    if (d.bs == 4) launch_bwd<float, float, 4>(d, d.y32, r, dot_mode, check_done, s, p);
-    else launch_bwd<float, float, 8>(d, d.y32, r, dot_mode, check_done, s, p);
+    if (d.bs == 4) launch_bwd<float, float, 4>(d, c, d.y32, r, dot_mode, check_done, part_off, last, part_total, s, p);
+    else launch_bwd<float, float, 8>(d, c, d.y32, r, dot_mode, check_done, part_off, last, part_total, s, p);
   }
 }
 

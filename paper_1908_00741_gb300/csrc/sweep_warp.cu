@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(32 * kMaxWpb)
 
 template <typename T, typename Y>
 __global__ void __launch_bounds__(32 * kMaxWpb)
-    k_bwd_w(const WArgs<T> a, const Y *__restrict__ yin, double *z, const double *__restrict__ r,
+    k_bwd_w(const WArgs<T> a, const Y *__restrict__ yin, double *z, float *z32, const double *__restrict__ r,
             Scalars *sc, int check_done, int dot_mode, double *part, int64_t part_off, int last_launch,
             int64_t part_total) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(32 * kMaxWpb)
     const WarpSmem<T> m = warp_smem(smem, a, warp);
     stage_unit<T, Y>(a, m, u, yin, lane);
     const int32_t *rs = m.rs;
-    run_accumulate<T, double, true>(a.o_col, a.o_val, z, rec64(rs, 2), rs[0], rs + 6, m.ts, lane);
+    run_accumulate<T, T, true>(a.o_col, a.o_val, zgather<T>(z, z32), rec64(rs, 2), rs[0], rs + 6, m.ts, lane);
     const int32_t *i_rel = rs + 7 + a.bs;
     for (int l = a.bs - 1; l >= 0; --l) {
       T acc = m.ts[(l << 5) + lane];
@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(32 * kMaxWpb)
     for (int l = 0; l < a.bs; ++l) {
       const double zv = (double)m.ts[(l << 5) + lane];
       z[row0 + (l << 5) + lane] = zv;
+      if constexpr (sizeof(T) == 4) z32[row0 + (l << 5) + lane] = m.ts[(l << 5) + lane];
       if (dot_mode) rz = fma(r[row0 + (l << 5) + lane], zv, rz);
     }
   }
@@ -331,10 +332,10 @@ void enqueue_bwd_warp(const DeviceLayout &d, int prec, const double *r, int dot_
     const unsigned grid = warp_grid(d.tile_ptr[c + 1] - d.tile_ptr[c], w.wpb);
     const int last = c == 0;
     if (prec == HBMC_PREC_F64)
-      k_bwd_w<double, double><<<grid, 32 * w.wpb, sm, s>>>(warp_args<double>(d, false, c, w), d.y, d.z, r, d.sc,
+      k_bwd_w<double, double><<<grid, 32 * w.wpb, sm, s>>>(warp_args<double>(d, false, c, w), d.y, d.z, d.z32, r, d.sc,
                                                            check_done ? 1 : 0, dot_mode, d.part, off, last, total);
     else
-      k_bwd_w<float, float><<<grid, 32 * w.wpb, sm, s>>>(warp_args<float>(d, false, c, w), d.y32, d.z, r, d.sc,
+      k_bwd_w<float, float><<<grid, 32 * w.wpb, sm, s>>>(warp_args<float>(d, false, c, w), d.y32, d.z, d.z32, r, d.sc,
                                                          check_done ? 1 : 0, dot_mode, d.part, off, last, total);
     off += grid;
   }

@@ -1,0 +1,355 @@
+// Substitution sweeps with one CUDA block of NT threads per
+// level-1 block, for colors that have few level-1 blocks.
+//
+// With one warp per level-1 block a color of U level-1 blocks runs U warps;
+// when U is near the SM count (matrices with many colors: a 27-point stencil
+// in a random order needs over 20) the GPU idles and each warp walks its
+// level-1 block's other-color couplings (Eq. "for3") a few entries per lane
+// at a time, one dependent trip to memory after another.  Here the whole
+// block does that walk at once:
+//   1. the level-1 block's record, right-hand side and dinv segments;
+//   2. every thread takes a share of the other-color run -- kWideU entries
+//      per round, column and coefficient loads first, then the gathers -- and
+//      parks coefficient and gathered value in shared memory; the same-block
+//      run is staged next to them;
+//   3. one thread per row adds its terms in the layout's order (farthest
+//      column from the diagonal first) out of shared memory;
+//   4. lanes j < w run the bs-step chains (Eqs. "y2-2", "y2-3");
+//   5. the rows are stored (backward: with the fused r.z).
+// The arithmetic and its order are those of every other sweep kernel, so
+// the results are bit-identical to them and to the oracle.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "hbmc_internal.h"
+#include "kernels.h"
+#include "warp_common.cuh"
+
+namespace hbmc {
+namespace {
+
+constexpr int kWideU = 8;
+constexpr size_t kWideSmemBudget = 200 * 1024;
+constexpr uint32_t kWideRecInts = 160;  // record of bs <= 64: 8 + 2 bs ints, rounded
+// Under automatic selection a color uses these kernels when its level-1
+// blocks' other-color runs are long -- a warp would walk at least
+// kWideMinRun entries, 8 per lane per trip to memory, one trip after
+// another -- or when it has fewer level-1 blocks than SMs.  Measured at
+// 128^3 (7-point, runs of 768 entries) the warp kernels win; on the 27-point
+// and 3-DOF matrices in a random order (runs of 5000-9000) these do.
+constexpr int64_t kWideMinRun = 2048;
+
+template <typename T>
+struct WideArgs {
+  const int32_t *rec;
+  const int32_t *o_col;
+  const T *o_val;
+  const uint8_t *i_m;
+  const T *i_val;
+  const T *dinv;
+  int rec_ints, bs, w, lw;
+  int64_t tile0;
+  uint32_t off_ts, off_ds, off_rr, off_vv, off_gv, off_iv, off_im;
+};
+
+template <int NT, bool FWD, typename T, typename IN, typename G, typename OUT>
+__device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *smem, int64_t u, const IN *in,
+                                          const G *gsrc, OUT *out, const double *r, bool dot, double &rz,
+                                          float *out32 = nullptr) {
+  int32_t *rs = reinterpret_cast<int32_t *>(smem);
+  T *ts = reinterpret_cast<T *>(smem + a.off_ts);
+  T *ds = reinterpret_cast<T *>(smem + a.off_ds);
+  double *rr = reinterpret_cast<double *>(smem + a.off_rr);
+  T *vv = reinterpret_cast<T *>(smem + a.off_vv);
+  T *gv = reinterpret_cast<T *>(smem + a.off_gv);
+  T *iv = reinterpret_cast<T *>(smem + a.off_iv);
+  uint8_t *im = smem + a.off_im;
+  const int tid = threadIdx.x;
+  const int R = a.bs << a.lw;
+  const int64_t row0 = u * (int64_t)R;
+  // 1.
+  const int32_t *rc = a.rec + u * a.rec_ints;
+  for (int k = tid; k < a.rec_ints; k += NT) rs[k] = rc[k];
+  for (int lr = tid; lr < R; lr += NT) {
+    ts[lr] = (T)in[row0 + lr];
+    ds[lr] = a.dinv[row0 + lr];
+    if (!FWD && dot) rr[lr] = r[row0 + lr];
+  }
+  __syncthreads();
+  const int olen = rs[0], ilen = rs[1];
+  const int64_t obeg = rec64(rs, 2), ibeg = rec64(rs, 4);
+  // 2.
+  for (int e0 = tid; e0 < olen; e0 += NT * kWideU) {
+    int32_t c[kWideU];
+    T v[kWideU], g[kWideU];
+#pragma unroll
+    for (int k = 0; k < kWideU; ++k) {
+      const int e = e0 + k * NT;
+      if (e < olen) {
+        c[k] = a.o_col[obeg + e];
+        v[k] = a.o_val[obeg + e];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kWideU; ++k)
+      if (e0 + k * NT < olen) g[k] = (T)gsrc[c[k]];
+#pragma unroll
+    for (int k = 0; k < kWideU; ++k) {
+      const int e = e0 + k * NT;
+      if (e < olen) {
+        vv[e] = v[k];
+        gv[e] = g[k];
+      }
+    }
+  }
+  for (int e = tid; e < ilen; e += NT) {
+    iv[e] = a.i_val[ibeg + e];
+    im[e] = a.i_m[ibeg + e];
+  }
+  __syncthreads();
+  // 3.
+  const int32_t *o_rel = rs + 6, *i_rel = rs + 7 + a.bs;
+  for (int lr = tid; lr < R; lr += NT) {
+    const int l = lr >> a.lw, j = lr & (a.w - 1);
+    T acc = ts[lr];
+    const int pe = o_rel[l + 1];
+    for (int p = o_rel[l] + j; p < pe; p += a.w) acc = fma(-vv[p], gv[p], acc);
+    ts[lr] = acc;
+  }
+  __syncthreads();
+  // 4.
+  if (tid < a.w) {
+    const int j = tid;
+    for (int q = 0; q < a.bs; ++q) {
+      const int l = FWD ? q : a.bs - 1 - q;
+      T acc = ts[(l << a.lw) + j];
+      const int pe = i_rel[l + 1];
+      for (int p = i_rel[l] + j; p < pe; p += a.w) acc = fma(-iv[p], ts[(im[p] << a.lw) + j], acc);
+      ts[(l << a.lw) + j] = acc * ds[(l << a.lw) + j];
+    }
+  }
+  __syncthreads();
+  // 5.
+  for (int lr = tid; lr < R; lr += NT) {
+    const T yv = ts[lr];
+    out[row0 + lr] = (OUT)yv;
+    if constexpr (!FWD && sizeof(T) == 4) out32[row0 + lr] = yv;
+    if (!FWD && dot) rz = fma(rr[lr], (double)yv, rz);
+  }
+}
+
+template <typename T, typename Y, int NT>
+__global__ void __launch_bounds__(NT)
+    k_fwd_wide(const WideArgs<T> a, const double *__restrict__ r, Y *y, const Scalars *sc, int check_done) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (check_done && sc->done) return;
+  double rz = 0.0;
+  wide_unit<NT, true, T, double, Y, Y>(a, smem, a.tile0 + blockIdx.x, r, y, y, nullptr, false, rz);
+}
+
+template <typename T, typename Y, int NT>
+__global__ void __launch_bounds__(NT)
+    k_bwd_wide(const WideArgs<T> a, const Y *__restrict__ yin, double *z, float *z32, const double *__restrict__ r,
+               Scalars *sc, int check_done, int dot_mode, double *part, int64_t part_off, int last_launch,
+               int64_t part_total) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (check_done && sc->done) return;
+  double rz = 0.0;
+  wide_unit<NT, false, T, Y, T, double>(a, smem, a.tile0 + blockIdx.x, yin, zgather<T>(z, z32), z, r, dot_mode != 0, rz,
+                                    z32);
+  if (!dot_mode) return;
+  const double v = block_sum_rt(rz);
+  if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
+  if (!last_launch) return;
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
+  const double rho_new = block_sum_rt(acc);
+  if (threadIdx.x != 0) return;
+  sc->cnt[CNT_RZ] = 0;
+  sc->rho_new = rho_new;
+  if (sc->timeout) return;
+  if (!(rho_new > 0.0) || !finite(rho_new)) {
+    sc->status = ST_BREAKDOWN;
+    sc->done = 1;
+    return;
+  }
+  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
+  sc->rho = rho_new;
+}
+
+uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
+
+WidePlan plan_one(int bs, int w, bool fwd, int rec_ints, int64_t max_o, int64_t max_i, size_t tsize) {
+  WidePlan p;
+  const uint64_t R = (uint64_t)bs * w;
+  p.off_ts = a16((uint64_t)kWideRecInts * 4);
+  p.off_ds = a16(p.off_ts + R * tsize);
+  p.off_rr = a16(p.off_ds + R * tsize);
+  p.off_vv = a16(p.off_rr + (fwd ? 0 : R * 8));
+  p.off_gv = a16(p.off_vv + (uint64_t)max_o * tsize);
+  p.off_iv = a16(p.off_gv + (uint64_t)max_o * tsize);
+  p.off_im = a16(p.off_iv + (uint64_t)max_i * tsize);
+  const uint64_t total = a16(p.off_im + (uint64_t)max_i);
+  p.smem_bytes = (uint32_t)std::min<uint64_t>(total, 0xffffffffu);
+  p.ok = rec_ints <= (int)kWideRecInts && total <= kWideSmemBudget;
+  return p;
+}
+
+const WidePlan &wide_plan(const DeviceLayout &d, bool fwd, int prec) {
+  return prec == HBMC_PREC_F64 ? (fwd ? d.wd_f64_f : d.wd_f64_b) : (fwd ? d.wd_f32_f : d.wd_f32_b);
+}
+
+template <typename T>
+WideArgs<T> wide_args(const DeviceLayout &d, bool fwd, int c, const WidePlan &p) {
+  WideArgs<T> a;
+  a.rec = fwd ? d.rec_f : d.rec_b;
+  a.rec_ints = d.rec_ints;
+  a.o_col = fwd ? d.fo_col : d.bo_col;
+  a.i_m = fwd ? d.fi_m : d.bi_m;
+  if constexpr (sizeof(T) == 8) {
+    a.o_val = (const T *)(fwd ? d.fo_val : d.bo_val);
+    a.i_val = (const T *)(fwd ? d.fi_val : d.bi_val);
+    a.dinv = (const T *)d.dinv;
+  } else {
+    a.o_val = (const T *)(fwd ? d.fo_val32 : d.bo_val32);
+    a.i_val = (const T *)(fwd ? d.fi_val32 : d.bi_val32);
+    a.dinv = (const T *)d.dinv32;
+  }
+  a.bs = d.bs;
+  a.w = d.w;
+  a.lw = d.lw;
+  a.tile0 = d.tile_ptr[c];
+  a.off_ts = p.off_ts;
+  a.off_ds = p.off_ds;
+  a.off_rr = p.off_rr;
+  a.off_vv = p.off_vv;
+  a.off_gv = p.off_gv;
+  a.off_iv = p.off_iv;
+  a.off_im = p.off_im;
+  return a;
+}
+
+template <typename K>
+cudaError_t allow(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWideSmemBudget);
+}
+
+}  // namespace
+
+void plan_wide_kernels(const HostLayout &h, DeviceLayout &d) {
+  for (int dir = 0; dir < 2; ++dir) {
+    const std::vector<int32_t> &rec = dir == 0 ? h.rec_f : h.rec_b;
+    std::vector<uint8_t> &pick = dir == 0 ? d.wide_f : d.wide_b;
+    pick.assign(h.nc, 0);
+    for (int c = 0; c < h.nc; ++c) {
+      const int64_t u0 = h.tile_ptr[c], u1 = h.tile_ptr[c + 1];
+      int64_t run = 0;
+      for (int64_t u = u0; u < u1; ++u) run += rec[(size_t)u * h.rec_ints];
+      const bool long_runs = u1 > u0 && run >= kWideMinRun * (u1 - u0);
+      pick[c] = (long_runs || u1 - u0 < d.sm_count) ? 1 : 0;
+    }
+  }
+  d.wd_f64_f = plan_one(h.bs, h.w, true, h.rec_ints, h.max_o_f, h.max_i_f, 8);
+  d.wd_f64_b = plan_one(h.bs, h.w, false, h.rec_ints, h.max_o_b, h.max_i_b, 8);
+  d.wd_f32_f = plan_one(h.bs, h.w, true, h.rec_ints, h.max_o_f, h.max_i_f, 4);
+  d.wd_f32_b = plan_one(h.bs, h.w, false, h.rec_ints, h.max_o_b, h.max_i_b, 4);
+}
+
+template <int NT>
+cudaError_t allow_nt() {
+  cudaError_t e;
+  if ((e = allow(k_fwd_wide<double, double, NT>)) || (e = allow(k_fwd_wide<float, float, NT>)) ||
+      (e = allow(k_bwd_wide<double, double, NT>)) || (e = allow(k_bwd_wide<float, float, NT>)))
+    return e;
+  return cudaSuccess;
+}
+
+cudaError_t setup_wide_kernels() {
+  cudaError_t e;
+  if ((e = allow_nt<256>()) || (e = allow_nt<512>()) || (e = allow_nt<1024>())) return e;
+  return cudaSuccess;
+}
+
+bool wide_usable(const DeviceLayout &d, bool fwd, int prec) {
+  return (d.sweep_kernel == 0 || d.sweep_kernel == 4) && d.rec_f && wide_plan(d, fwd, prec).ok;
+}
+
+bool wide_preferred(const DeviceLayout &d, bool fwd, int c) {
+  if (d.sweep_kernel == 4) return true;
+  if (d.sweep_kernel != 0) return false;
+  const std::vector<uint8_t> &v = fwd ? d.wide_f : d.wide_b;
+  return c < (int)v.size() && v[c] != 0;
+}
+
+unsigned wide_color_grid(const DeviceLayout &d, int c) { return (unsigned)(d.tile_ptr[c + 1] - d.tile_ptr[c]); }
+
+// Threads per level-1 block: all 1024 when the color has about one level-1
+// block per SM, fewer when several share an SM.
+static int wide_threads(const DeviceLayout &d, int c) {
+  const int64_t per_sm = (wide_color_grid(d, c) + d.sm_count - 1) / d.sm_count;
+  return per_sm <= 1 ? 1024 : per_sm <= 2 ? 512 : 256;
+}
+
+template <typename T, typename Y, int NT>
+void fwd_nt(const DeviceLayout &d, int c, const double *r, Y *y, bool check_done, cudaStream_t s, const WidePlan &p) {
+  k_fwd_wide<T, Y, NT><<<wide_color_grid(d, c), NT, p.smem_bytes, s>>>(wide_args<T>(d, true, c, p), r, y, d.sc,
+                                                                        check_done ? 1 : 0);
+}
+
+template <typename T, typename Y, int NT>
+void bwd_nt(const DeviceLayout &d, int c, const Y *yin, const double *r, int dot_mode, bool check_done,
+            int64_t part_off, bool last, int64_t part_total, cudaStream_t s, const WidePlan &p) {
+  k_bwd_wide<T, Y, NT><<<wide_color_grid(d, c), NT, p.smem_bytes, s>>>(
+      wide_args<T>(d, false, c, p), yin, d.z, d.z32, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, part_off,
+      last ? 1 : 0, part_total);
+}
+
+template <typename T, typename Y>
+void fwd_any(const DeviceLayout &d, int c, const double *r, Y *y, bool check_done, cudaStream_t s,
+             const WidePlan &p) {
+  switch (wide_threads(d, c)) {
+    case 1024: fwd_nt<T, Y, 1024>(d, c, r, y, check_done, s, p); break;
+    case 512: fwd_nt<T, Y, 512>(d, c, r, y, check_done, s, p); break;
+    default: fwd_nt<T, Y, 256>(d, c, r, y, check_done, s, p); break;
+  }
+}
+
+template <typename T, typename Y>
+void bwd_any(const DeviceLayout &d, int c, const Y *yin, const double *r, int dot_mode, bool check_done,
+             int64_t part_off, bool last, int64_t part_total, cudaStream_t s, const WidePlan &p) {
+  switch (wide_threads(d, c)) {
+    case 1024: bwd_nt<T, Y, 1024>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
+    case 512: bwd_nt<T, Y, 512>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
+    default: bwd_nt<T, Y, 256>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
+  }
+}
+
+void launch_fwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done,
+                           cudaStream_t s) {
+  if (wide_color_grid(d, c) == 0) return;
+  const WidePlan &p = wide_plan(d, true, prec);
+  if (prec == HBMC_PREC_F64) fwd_any<double, double>(d, c, r, d.y, check_done, s, p);
+  else fwd_any<float, float>(d, c, r, d.y32, check_done, s, p);
+}
+
+void launch_bwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
+                           int64_t part_off, bool last, int64_t part_total, cudaStream_t s) {
+  if (wide_color_grid(d, c) == 0) return;
+  const WidePlan &p = wide_plan(d, false, prec);
+  if (prec == HBMC_PREC_F64) bwd_any<double, double>(d, c, d.y, r, dot_mode, check_done, part_off, last, part_total, s, p);
+  else bwd_any<float, float>(d, c, d.y32, r, dot_mode, check_done, part_off, last, part_total, s, p);
+}
+
+}  // namespace hbmc

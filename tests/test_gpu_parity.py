@@ -349,13 +349,14 @@ def test_sweep_geometry_variants_bitwise(lib, orc, tpb, w, bs):
 @pytest.mark.parametrize("name,mk,bs,w,box", [c for c in CASES if c[3] == 32])
 @pytest.mark.parametrize("precision", [H.PREC_F64, H.PREC_F32])
 def test_sweep_kernel_variants_agree(lib, orc, name, mk, bs, w, box, precision):
-    """The warp-per-unit kernels (default for w = 32; runs staged by bulk
-    copy for bs 4 and 8, plain loads with sweep_kernel 3), the
-    block-per-unit kernels and the TMA-fed kernels compute the same bits, in
-    both precisions, and FP64 matches the oracle."""
+    """Every substitution kernel computes the same bits, in both precisions,
+    and FP64 matches the oracle: 0 automatic (loader-thread blocks for these
+    small colors), 1 block per level-1 block, 2 TMA-fed persistent, 3 warp
+    per level-1 block with plain loads, 4 loader-thread blocks, 5 warp per
+    level-1 block staged by bulk copy (bs 4 and 8)."""
     A = mk()
     outs = []
-    for sk in (0, 1, 2, 3):
+    for sk in (0, 1, 2, 3, 4, 5):
         ctx = H.hbmc_build(A, bs, w, box=box, sweep_kernel=sk, precision=precision)
         assert H.hbmc_ic0(ctx, 0.1)[0] == H.OK
         n_pad = ctx.info()["n_pad"]
