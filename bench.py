@@ -535,6 +535,59 @@ def run_learned(args):
 # reference arm: the CPU oracle
 # --------------------------------------------------------------------------
 
+def run_orderings(args):
+    """The paper's comparison (Section 5, Tables "number-ite" and "Results")
+    on the 128^3 7-point workload with the library's own kernels: MC = nodal
+    multi-color ordering (blocks of one unknown, bs = 1, w = 32); BMC = block
+    multi-color without the secondary reordering (bs = 8, w = 1: a level-1
+    block is one BMC block, so pi_HBMC = pi_BMC); HBMC (bs = 8, w = 32).  FP64
+    throughout; iterations, ms per solve and us per CG iteration."""
+    import torch
+    from paper_1908_00741_gb300 import hbmc as H
+    from paper_1908_00741_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    with ClockSampler(local) as clk:
+        for name, bs, w in (("MC", 1, 32), ("BMC", 8, 1), ("HBMC", 8, 32)):
+            P = W.poisson_problem(GRID, bs=bs)
+            ctx = H.hbmc_build(P.A, bs, w, box=P.box, device=local)
+            H.hbmc_set_stream(ctx, stream)
+            assert H.hbmc_ic0(ctx)[0] == H.OK
+            b = torch.tensor(P.b, device="cuda")
+            x = torch.zeros_like(b)
+            for _ in range(args.warmup):
+                x.zero_()
+                res = H.hbmc_iccg(ctx, b, x, tol=TOL, maxit=10000)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(args.steps):
+                x.zero_()
+                res = H.hbmc_iccg(ctx, b, x, tol=TOL, maxit=10000)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / args.steps
+            inf = ctx.info()
+            rows[name] = {"bs": bs, "w": w, "colors": inf["nc"], "iters": res.iters, "status": res.status,
+                          "true_relres": res.true_relres, "ms": round(ms, 3),
+                          "us_per_iter": round(ms * 1e3 / max(res.iters, 1), 1)}
+            ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "ICCG time to 1e-8 FP64 residual under MC, BMC and HBMC orderings", "value": rows["HBMC"]["ms"],
+        "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": rows["HBMC"]["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"7-point Poisson {GRID}^3, natural input order; MC bs=1 w=32, BMC bs=8 w=1, "
+                               f"HBMC bs=8 w=32 (2x2x2 boxes)"},
+        "orderings": rows, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -581,9 +634,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--bs", type=int, default=DEFAULT_BS)
-    ap.add_argument("--workload", default="poisson128", choices=["poisson128", "batch", "learned"],
+    ap.add_argument("--workload", default="poisson128", choices=["poisson128", "batch", "learned", "orderings"],
                     help="poisson128: the headline solve; batch: 256 uneven systems solved together; "
-                         "learned: learned IC shift against the plain rule")
+                         "learned: learned IC shift against the plain rule; orderings: MC, BMC and HBMC")
     ap.add_argument("--learned-train", type=int, default=200)
     ap.add_argument("--learned-heldout", type=int, default=40)
     ap.add_argument("--veclap-m", type=int, default=100)
@@ -606,7 +659,7 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build()
-        {"batch": run_batch, "learned": run_learned}.get(args.workload, run_gpu)(args)
+        {"batch": run_batch, "learned": run_learned, "orderings": run_orderings}.get(args.workload, run_gpu)(args)
 
 
 if __name__ == "__main__":

@@ -383,3 +383,26 @@ def test_sweep_kernel_variants_agree(lib, orc, name, mk, bs, w, box, precision):
         lval, _, dinv, _ = orc.factor(an, 0.1)
         np.testing.assert_array_equal(outs[0][0], orc.fwd(an.row_ptr, an.col, lval, dinv, r))
         np.testing.assert_array_equal(outs[0][4], orc.spmv(an.row_ptr, an.col, an.val, r))
+
+
+def test_mc_bmc_hbmc_orderings(lib, orc):
+    """The paper's comparison with the library's kernels (Section 5): BMC
+    (w = 1, pi_HBMC = pi_BMC) and HBMC (w = 32) with the same blocks and
+    colors take the same number of iterations (Section 4.2.1's equivalence)
+    and agree with the oracle; nodal MC (bs = 1) needs more iterations than
+    either on the 7-point stencil."""
+    A = W.poisson7(16)
+    b, _ = W.rhs_from_solution(A, 0)
+    out = {}
+    for name, bs, w in (("MC", 1, 32), ("BMC", 8, 1), ("HBMC", 8, 32)):
+        box = W.box_for_bs(bs)
+        ctx, an, lval, ldiag, dinv = _setup(orc, A, bs, w, box)
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        res = H.hbmc_iccg(ctx, dev(b), x, tol=1e-8)
+        ref = orc.pcg(an, lval, dinv, b, tol=1e-8)
+        assert res.status == H.OK and res.iters == ref.iters
+        assert _rel(host(x), ref.x) <= 1e-12
+        out[name] = (res.iters, host(x))
+    assert out["BMC"][0] == out["HBMC"][0]
+    assert _rel(out["BMC"][1], out["HBMC"][1]) <= 1e-12
+    assert out["MC"][0] > out["HBMC"][0]
