@@ -90,8 +90,12 @@ typedef struct hbmc_options {
                            4 = one CUDA block of loader threads per level-1 block for every
                                color (automatic under 0, when bs is 4 or 8 and w = 32, for
                                colors whose level-1 blocks average 2048 or more other-color
-                               couplings or that have fewer level-1 blocks than SMs);
-                           5 = the bulk-copy-staged warp kernels of 0 for every color. 
+                               couplings or that have fewer than two level-1 blocks per SM;
+                               runs staged by bulk copy when w = 32 and that costs no extra
+                               wave of CUDA blocks);
+                           5 = the bulk-copy-staged warp kernels of 0 for every color;
+                           6 = as 4 with the runs read by plain loads instead of bulk
+                               copies (the form 4 uses when w < 32). 
                            SpMV (w = 32) is fed by bulk copies when a chunk of its slices fits
                            in shared memory, else one thread per row; with 3 it runs one warp
                            per level-1 block. */

@@ -364,8 +364,8 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
   if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown loop mode");
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 5)
-    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..5");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 6)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..6");
   if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_tpb must be 0 or a power of two with sweep_tpb * w <= 256");
   hbmc_ctx *ctx = nullptr;

@@ -138,7 +138,8 @@ struct TwPlan {
 // Shared memory of the loader-thread sweeps (sweep_wide.cu), byte offsets;
 // ok = false when a level-1 block's runs do not fit.
 struct WidePlan {
-  uint32_t off_ts = 0, off_ds = 0, off_rr = 0, off_vv = 0, off_gv = 0, off_iv = 0, off_im = 0, smem_bytes = 0;
+  uint32_t off_ts = 0, off_tin = 0, off_ds = 0, off_rr = 0, off_oc = 0, off_vv = 0, off_gv = 0, off_iv = 0,
+           off_im = 0, smem_bytes = 0;
   bool ok = false;
 };
 
@@ -181,7 +182,8 @@ struct DeviceLayout {
   WarpPlan wp_f64_f, wp_f64_b, wp_f32_f, wp_f32_b, wp_spmv;
   TwPlan tw_f64_f, tw_f64_b, tw_f32_f, tw_f32_b;
   SpmvPlan sp;
-  WidePlan wd_f64_f, wd_f64_b, wd_f32_f, wd_f32_b;
+  WidePlan wd_f64_f, wd_f64_b, wd_f32_f, wd_f32_b;  // plain-load staging
+  WidePlan wt_f64_f, wt_f64_b, wt_f32_f, wt_f32_b;  // bulk-copy staging (w = 32)
   std::vector<uint8_t> wide_f, wide_b;  // per color: the loader-thread sweep is the faster one
   int32_t lw = 0;        // log2(w)
   int64_t max_in_f = 0, max_in_b = 0;

@@ -608,7 +608,7 @@ void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, c
 // bulk-copy-staged warp kernel; both give the same bits.
 void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
   const bool wide = wide_usable(d, true, prec), tw = tw_usable(d, true, prec);
-  if ((wide && d.sweep_kernel == 4) || tw) {
+  if ((wide && wide_all(d)) || tw) {
     for (int c = 0; c < d.nc; ++c) {
       if (wide && wide_preferred(d, true, c)) launch_fwd_wide_color(d, prec, c, r, check_done, s);
       else launch_fwd_tw_color(d, prec, c, r, check_done, s);
@@ -633,7 +633,7 @@ void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_do
 // dot, 1: initial rho = r.z, 2: rho and beta.
 void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s) {
   const bool wide = wide_usable(d, false, prec), tw = tw_usable(d, false, prec);
-  if ((wide && d.sweep_kernel == 4) || tw) {
+  if ((wide && wide_all(d)) || tw) {
     auto use_wide = [&](int c) { return wide && wide_preferred(d, false, c); };
     int64_t total = 0;
     for (int c = 0; c < d.nc; ++c) total += use_wide(c) ? wide_color_grid(d, c) : tw_color_grid(d, c);

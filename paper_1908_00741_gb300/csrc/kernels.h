@@ -39,6 +39,7 @@ void launch_bwd_tw_color(const DeviceLayout &d, int prec, int c, const double *r
 void plan_wide_kernels(const HostLayout &h, DeviceLayout &d);
 cudaError_t setup_wide_kernels();
 bool wide_usable(const DeviceLayout &d, bool fwd, int prec);
+bool wide_all(const DeviceLayout &d);
 bool wide_preferred(const DeviceLayout &d, bool fwd, int c);
 unsigned wide_color_grid(const DeviceLayout &d, int c);
 void launch_fwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done, cudaStream_t s);

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "hbmc_internal.h"
@@ -34,10 +35,12 @@ namespace {
 constexpr int kWideU = 8;
 constexpr size_t kWideSmemBudget = 200 * 1024;
 constexpr uint32_t kWideRecInts = 160;  // record of bs <= 64: 8 + 2 bs ints, rounded
+constexpr uint32_t kWideRecOff = 16;    // record after the bulk-copy variant's mbarrier
+constexpr uint64_t kWideWaitNs = 4000000000ull;
 // Under automatic selection a color uses these kernels when its level-1
 // blocks' other-color runs are long -- a warp would walk at least
 // kWideMinRun entries, 8 per lane per trip to memory, one trip after
-// another -- or when it has fewer level-1 blocks than SMs.  Measured at
+// another -- or when it has fewer than two level-1 blocks per SM.  Measured at
 // 128^3 (7-point, runs of 768 entries) the warp kernels win; on the 27-point
 // and 3-DOF matrices in a random order (runs of 5000-9000) these do.
 constexpr int64_t kWideMinRun = 2048;
@@ -52,14 +55,60 @@ struct WideArgs {
   const T *dinv;
   int rec_ints, bs, w, lw;
   int64_t tile0;
-  uint32_t off_ts, off_ds, off_rr, off_vv, off_gv, off_iv, off_im;
+  uint32_t off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_gv, off_iv, off_im;
 };
+
+// Phases 3-5, common to both ways of staging: in-order sums of the
+// other-color terms out of shared memory, the bs-step chains, the stores.
+template <int NT, bool FWD, typename T, typename OUT>
+__device__ __forceinline__ void wide_finish(const WideArgs<T> &a, unsigned char *smem, int64_t row0, OUT *out,
+                                            bool dot, double &rz, float *out32) {
+  const int32_t *rs = reinterpret_cast<const int32_t *>(smem + kWideRecOff);
+  T *ts = reinterpret_cast<T *>(smem + a.off_ts);
+  const T *ds = reinterpret_cast<const T *>(smem + a.off_ds);
+  const double *rr = reinterpret_cast<const double *>(smem + a.off_rr);
+  const T *vv = reinterpret_cast<const T *>(smem + a.off_vv);
+  const T *gv = reinterpret_cast<const T *>(smem + a.off_gv);
+  const T *iv = reinterpret_cast<const T *>(smem + a.off_iv);
+  const uint8_t *im = smem + a.off_im;
+  const int tid = threadIdx.x;
+  const int R = a.bs << a.lw;
+  // 3.
+  const int32_t *o_rel = rs + 6, *i_rel = rs + 7 + a.bs;
+  for (int lr = tid; lr < R; lr += NT) {
+    const int l = lr >> a.lw, j = lr & (a.w - 1);
+    T acc = ts[lr];
+    const int pe = o_rel[l + 1];
+    for (int p = o_rel[l] + j; p < pe; p += a.w) acc = fma(-vv[p], gv[p], acc);
+    ts[lr] = acc;
+  }
+  __syncthreads();
+  // 4.
+  if (tid < a.w) {
+    const int j = tid;
+    for (int q = 0; q < a.bs; ++q) {
+      const int l = FWD ? q : a.bs - 1 - q;
+      T acc = ts[(l << a.lw) + j];
+      const int pe = i_rel[l + 1];
+      for (int p = i_rel[l] + j; p < pe; p += a.w) acc = fma(-iv[p], ts[(im[p] << a.lw) + j], acc);
+      ts[(l << a.lw) + j] = acc * ds[(l << a.lw) + j];
+    }
+  }
+  __syncthreads();
+  // 5.
+  for (int lr = tid; lr < R; lr += NT) {
+    const T yv = ts[lr];
+    out[row0 + lr] = (OUT)yv;
+    if constexpr (!FWD && sizeof(T) == 4) out32[row0 + lr] = yv;
+    if (!FWD && dot) rz = fma(rr[lr], (double)yv, rz);
+  }
+}
 
 template <int NT, bool FWD, typename T, typename IN, typename G, typename OUT>
 __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *smem, int64_t u, const IN *in,
                                           const G *gsrc, OUT *out, const double *r, bool dot, double &rz,
                                           float *out32 = nullptr) {
-  int32_t *rs = reinterpret_cast<int32_t *>(smem);
+  int32_t *rs = reinterpret_cast<int32_t *>(smem + kWideRecOff);
   T *ts = reinterpret_cast<T *>(smem + a.off_ts);
   T *ds = reinterpret_cast<T *>(smem + a.off_ds);
   double *rr = reinterpret_cast<double *>(smem + a.off_rr);
@@ -110,56 +159,111 @@ __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *s
     im[e] = a.i_m[ibeg + e];
   }
   __syncthreads();
-  // 3.
-  const int32_t *o_rel = rs + 6, *i_rel = rs + 7 + a.bs;
-  for (int lr = tid; lr < R; lr += NT) {
-    const int l = lr >> a.lw, j = lr & (a.w - 1);
-    T acc = ts[lr];
-    const int pe = o_rel[l + 1];
-    for (int p = o_rel[l] + j; p < pe; p += a.w) acc = fma(-vv[p], gv[p], acc);
-    ts[lr] = acc;
+  wide_finish<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
+}
+
+// The same with w = 32 and every contiguous operand moved by bulk copy
+// (cp.async.bulk onto one mbarrier): right-hand side, dinv and r start with
+// the record load; the record then gives the runs -- columns and coefficients
+// of the other-color run, the same-block run -- and the only loads left to
+// the threads are the gathers.  Three dependent trips to memory in all.
+// Returns false when the bounded wait ran out (the solve is then stopped).
+template <int NT, bool FWD, typename T, typename IN, typename G, typename OUT>
+__device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned char *smem, int64_t u, const IN *in,
+                                              const G *gsrc, OUT *out, const double *r, bool dot, double &rz,
+                                              Scalars *sc, float *out32 = nullptr) {
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int32_t *rs = reinterpret_cast<int32_t *>(smem + kWideRecOff);
+  T *ts = reinterpret_cast<T *>(smem + a.off_ts);
+  IN *tin = reinterpret_cast<IN *>(smem + a.off_tin);  // == ts when IN is T
+  T *ds = reinterpret_cast<T *>(smem + a.off_ds);
+  double *rr = reinterpret_cast<double *>(smem + a.off_rr);
+  int32_t *oc = reinterpret_cast<int32_t *>(smem + a.off_oc);
+  T *vv = reinterpret_cast<T *>(smem + a.off_vv);
+  T *gv = reinterpret_cast<T *>(smem + a.off_gv);
+  T *iv = reinterpret_cast<T *>(smem + a.off_iv);
+  uint8_t *im = smem + a.off_im;
+  const int tid = threadIdx.x;
+  const uint32_t R = (uint32_t)a.bs * 32u;
+  const int64_t row0 = u * (int64_t)R;
+  const bool want_r = !FWD && dot;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    mbar_expect_tx(bar, R * (uint32_t)(sizeof(IN) + sizeof(T)) + (want_r ? R * 8u : 0u));
+    tma_load_1d(tin, in + row0, R * (uint32_t)sizeof(IN), bar);
+    tma_load_1d(ds, a.dinv + row0, R * (uint32_t)sizeof(T), bar);
+    if (want_r) tma_load_1d(rr, r + row0, R * 8u, bar);
   }
+  const int32_t *rc = a.rec + u * a.rec_ints;
+  for (int k = tid; k < a.rec_ints; k += NT) rs[k] = rc[k];
   __syncthreads();
-  // 4.
-  if (tid < a.w) {
-    const int j = tid;
-    for (int q = 0; q < a.bs; ++q) {
-      const int l = FWD ? q : a.bs - 1 - q;
-      T acc = ts[(l << a.lw) + j];
-      const int pe = i_rel[l + 1];
-      for (int p = i_rel[l] + j; p < pe; p += a.w) acc = fma(-iv[p], ts[(im[p] << a.lw) + j], acc);
-      ts[(l << a.lw) + j] = acc * ds[(l << a.lw) + j];
+  const int olen = rs[0], ilen = rs[1];
+  const int64_t obeg = rec64(rs, 2), ibeg = rec64(rs, 4);
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)olen * (uint32_t)(4 + sizeof(T)) + (uint32_t)ilen * (uint32_t)(1 + sizeof(T)));
+    if (olen > 0) {
+      tma_load_1d(oc, a.o_col + obeg, (uint32_t)olen * 4u, bar);
+      tma_load_1d(vv, a.o_val + obeg, (uint32_t)olen * (uint32_t)sizeof(T), bar);
+    }
+    if (ilen > 0) {
+      tma_load_1d(iv, a.i_val + ibeg, (uint32_t)ilen * (uint32_t)sizeof(T), bar);
+      tma_load_1d(im, a.i_m + ibeg, (uint32_t)ilen, bar);
     }
   }
-  __syncthreads();
-  // 5.
-  for (int lr = tid; lr < R; lr += NT) {
-    const T yv = ts[lr];
-    out[row0 + lr] = (OUT)yv;
-    if constexpr (!FWD && sizeof(T) == 4) out32[row0 + lr] = yv;
-    if (!FWD && dot) rz = fma(rr[lr], (double)yv, rz);
+  const uint64_t deadline = global_ns() + kWideWaitNs;
+  if (!__syncthreads_and(mbar_wait(bar, 0, deadline) ? 1 : 0)) {
+    if (tid == 0) {
+      sc->timeout = 1;
+      sc->done = 1;
+      mbar_wait(bar, 0, deadline + kWideWaitNs);  // let the copies land before the block leaves
+    }
+    __syncthreads();
+    return false;
   }
+  if constexpr (!std::is_same<IN, T>::value) {
+    for (int lr = tid; lr < (int)R; lr += NT) ts[lr] = (T)tin[lr];
+  }
+  for (int e0 = tid; e0 < olen; e0 += NT * kWideU) {
+    T g[kWideU];
+#pragma unroll
+    for (int k = 0; k < kWideU; ++k)
+      if (e0 + k * NT < olen) g[k] = (T)gsrc[oc[e0 + k * NT]];
+#pragma unroll
+    for (int k = 0; k < kWideU; ++k)
+      if (e0 + k * NT < olen) gv[e0 + k * NT] = g[k];
+  }
+  __syncthreads();
+  wide_finish<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
+  return true;
 }
 
-template <typename T, typename Y, int NT>
+template <typename T, typename Y, int NT, bool TMA>
 __global__ void __launch_bounds__(NT)
-    k_fwd_wide(const WideArgs<T> a, const double *__restrict__ r, Y *y, const Scalars *sc, int check_done) {
-  extern __shared__ __align__(16) unsigned char smem[];
+    k_fwd_wide(const WideArgs<T> a, const double *__restrict__ r, Y *y, Scalars *sc, int check_done) {
+  extern __shared__ __align__(128) unsigned char smem[];
   if (check_done && sc->done) return;
   double rz = 0.0;
-  wide_unit<NT, true, T, double, Y, Y>(a, smem, a.tile0 + blockIdx.x, r, y, y, nullptr, false, rz);
+  if constexpr (TMA)
+    wide_unit_tma<NT, true, T, double, Y, Y>(a, smem, a.tile0 + blockIdx.x, r, y, y, nullptr, false, rz, sc);
+  else
+    wide_unit<NT, true, T, double, Y, Y>(a, smem, a.tile0 + blockIdx.x, r, y, y, nullptr, false, rz);
 }
 
-template <typename T, typename Y, int NT>
+template <typename T, typename Y, int NT, bool TMA>
 __global__ void __launch_bounds__(NT)
     k_bwd_wide(const WideArgs<T> a, const Y *__restrict__ yin, double *z, float *z32, const double *__restrict__ r,
                Scalars *sc, int check_done, int dot_mode, double *part, int64_t part_off, int last_launch,
                int64_t part_total) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   if (check_done && sc->done) return;
   double rz = 0.0;
-  wide_unit<NT, false, T, Y, T, double>(a, smem, a.tile0 + blockIdx.x, yin, zgather<T>(z, z32), z, r, dot_mode != 0, rz,
-                                    z32);
+  if constexpr (TMA)
+    wide_unit_tma<NT, false, T, Y, T, double>(a, smem, a.tile0 + blockIdx.x, yin, zgather<T>(z, z32), z, r,
+                                              dot_mode != 0, rz, sc, z32);
+  else
+    wide_unit<NT, false, T, Y, T, double>(a, smem, a.tile0 + blockIdx.x, yin, zgather<T>(z, z32), z, r,
+                                          dot_mode != 0, rz, z32);
   if (!dot_mode) return;
   const double v = block_sum_rt(rz);
   if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
@@ -191,24 +295,38 @@ __global__ void __launch_bounds__(NT)
 
 uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
 
-WidePlan plan_one(int bs, int w, bool fwd, int rec_ints, int64_t max_o, int64_t max_i, size_t tsize) {
+// Shared-memory plan: plain-load staging (tma = false) or bulk-copy staging
+// (tma = true, w = 32; adds the column run and, for FP32 forward sweeps, a
+// double landing area for r).
+WidePlan plan_one(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o, int64_t max_i, size_t tsize) {
   WidePlan p;
   const uint64_t R = (uint64_t)bs * w;
-  p.off_ts = a16((uint64_t)kWideRecInts * 4);
-  p.off_ds = a16(p.off_ts + R * tsize);
+  p.off_ts = a16((uint64_t)kWideRecOff + (uint64_t)kWideRecInts * 4);
+  uint64_t next = p.off_ts + R * tsize;
+  p.off_tin = p.off_ts;
+  if (tma && fwd && tsize != 8) {
+    p.off_tin = a16(next);
+    next = p.off_tin + R * 8;
+  }
+  p.off_ds = a16(next);
   p.off_rr = a16(p.off_ds + R * tsize);
-  p.off_vv = a16(p.off_rr + (fwd ? 0 : R * 8));
+  p.off_oc = a16(p.off_rr + (fwd ? 0 : R * 8));
+  p.off_vv = a16(p.off_oc + (tma ? (uint64_t)max_o * 4 : 0));
   p.off_gv = a16(p.off_vv + (uint64_t)max_o * tsize);
   p.off_iv = a16(p.off_gv + (uint64_t)max_o * tsize);
   p.off_im = a16(p.off_iv + (uint64_t)max_i * tsize);
   const uint64_t total = a16(p.off_im + (uint64_t)max_i);
   p.smem_bytes = (uint32_t)std::min<uint64_t>(total, 0xffffffffu);
-  p.ok = rec_ints <= (int)kWideRecInts && total <= kWideSmemBudget;
+  p.ok = rec_ints <= (int)kWideRecInts && total <= kWideSmemBudget && (!tma || w == 32);
   return p;
 }
 
 const WidePlan &wide_plan(const DeviceLayout &d, bool fwd, int prec) {
   return prec == HBMC_PREC_F64 ? (fwd ? d.wd_f64_f : d.wd_f64_b) : (fwd ? d.wd_f32_f : d.wd_f32_b);
+}
+
+const WidePlan &wide_tma_plan(const DeviceLayout &d, bool fwd, int prec) {
+  return prec == HBMC_PREC_F64 ? (fwd ? d.wt_f64_f : d.wt_f64_b) : (fwd ? d.wt_f32_f : d.wt_f32_b);
 }
 
 template <typename T>
@@ -232,8 +350,10 @@ WideArgs<T> wide_args(const DeviceLayout &d, bool fwd, int c, const WidePlan &p)
   a.lw = d.lw;
   a.tile0 = d.tile_ptr[c];
   a.off_ts = p.off_ts;
+  a.off_tin = p.off_tin;
   a.off_ds = p.off_ds;
   a.off_rr = p.off_rr;
+  a.off_oc = p.off_oc;
   a.off_vv = p.off_vv;
   a.off_gv = p.off_gv;
   a.off_iv = p.off_iv;
@@ -258,36 +378,42 @@ void plan_wide_kernels(const HostLayout &h, DeviceLayout &d) {
       int64_t run = 0;
       for (int64_t u = u0; u < u1; ++u) run += rec[(size_t)u * h.rec_ints];
       const bool long_runs = u1 > u0 && run >= kWideMinRun * (u1 - u0);
-      pick[c] = (long_runs || u1 - u0 < d.sm_count) ? 1 : 0;
+      pick[c] = (long_runs || u1 - u0 < 2 * (int64_t)d.sm_count) ? 1 : 0;
     }
   }
-  d.wd_f64_f = plan_one(h.bs, h.w, true, h.rec_ints, h.max_o_f, h.max_i_f, 8);
-  d.wd_f64_b = plan_one(h.bs, h.w, false, h.rec_ints, h.max_o_b, h.max_i_b, 8);
-  d.wd_f32_f = plan_one(h.bs, h.w, true, h.rec_ints, h.max_o_f, h.max_i_f, 4);
-  d.wd_f32_b = plan_one(h.bs, h.w, false, h.rec_ints, h.max_o_b, h.max_i_b, 4);
+  for (int tma = 0; tma < 2; ++tma) {
+    (tma ? d.wt_f64_f : d.wd_f64_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, 8);
+    (tma ? d.wt_f64_b : d.wd_f64_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, 8);
+    (tma ? d.wt_f32_f : d.wd_f32_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, 4);
+    (tma ? d.wt_f32_b : d.wd_f32_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, 4);
+  }
 }
 
-template <int NT>
+template <int NT, bool TMA>
 cudaError_t allow_nt() {
   cudaError_t e;
-  if ((e = allow(k_fwd_wide<double, double, NT>)) || (e = allow(k_fwd_wide<float, float, NT>)) ||
-      (e = allow(k_bwd_wide<double, double, NT>)) || (e = allow(k_bwd_wide<float, float, NT>)))
+  if ((e = allow(k_fwd_wide<double, double, NT, TMA>)) || (e = allow(k_fwd_wide<float, float, NT, TMA>)) ||
+      (e = allow(k_bwd_wide<double, double, NT, TMA>)) || (e = allow(k_bwd_wide<float, float, NT, TMA>)))
     return e;
   return cudaSuccess;
 }
 
 cudaError_t setup_wide_kernels() {
   cudaError_t e;
-  if ((e = allow_nt<256>()) || (e = allow_nt<512>()) || (e = allow_nt<1024>())) return e;
+  if ((e = allow_nt<256, false>()) || (e = allow_nt<512, false>()) || (e = allow_nt<1024, false>()) ||
+      (e = allow_nt<256, true>()) || (e = allow_nt<512, true>()) || (e = allow_nt<1024, true>()))
+    return e;
   return cudaSuccess;
 }
 
+bool wide_all(const DeviceLayout &d) { return d.sweep_kernel == 4 || d.sweep_kernel == 6; }
+
 bool wide_usable(const DeviceLayout &d, bool fwd, int prec) {
-  return (d.sweep_kernel == 0 || d.sweep_kernel == 4) && d.rec_f && wide_plan(d, fwd, prec).ok;
+  return (d.sweep_kernel == 0 || wide_all(d)) && d.rec_f && wide_plan(d, fwd, prec).ok;
 }
 
 bool wide_preferred(const DeviceLayout &d, bool fwd, int c) {
-  if (d.sweep_kernel == 4) return true;
+  if (wide_all(d)) return true;
   if (d.sweep_kernel != 0) return false;
   const std::vector<uint8_t> &v = fwd ? d.wide_f : d.wide_b;
   return c < (int)v.size() && v[c] != 0;
@@ -302,54 +428,89 @@ static int wide_threads(const DeviceLayout &d, int c) {
   return per_sm <= 1 ? 1024 : per_sm <= 2 ? 512 : 256;
 }
 
-template <typename T, typename Y, int NT>
+template <typename T, typename Y, int NT, bool TMA>
 void fwd_nt(const DeviceLayout &d, int c, const double *r, Y *y, bool check_done, cudaStream_t s, const WidePlan &p) {
-  k_fwd_wide<T, Y, NT><<<wide_color_grid(d, c), NT, p.smem_bytes, s>>>(wide_args<T>(d, true, c, p), r, y, d.sc,
-                                                                        check_done ? 1 : 0);
+  k_fwd_wide<T, Y, NT, TMA><<<wide_color_grid(d, c), NT, p.smem_bytes, s>>>(wide_args<T>(d, true, c, p), r, y, d.sc,
+                                                                             check_done ? 1 : 0);
 }
 
-template <typename T, typename Y, int NT>
+template <typename T, typename Y, int NT, bool TMA>
 void bwd_nt(const DeviceLayout &d, int c, const Y *yin, const double *r, int dot_mode, bool check_done,
             int64_t part_off, bool last, int64_t part_total, cudaStream_t s, const WidePlan &p) {
-  k_bwd_wide<T, Y, NT><<<wide_color_grid(d, c), NT, p.smem_bytes, s>>>(
+  k_bwd_wide<T, Y, NT, TMA><<<wide_color_grid(d, c), NT, p.smem_bytes, s>>>(
       wide_args<T>(d, false, c, p), yin, d.z, d.z32, r, d.sc, check_done ? 1 : 0, dot_mode, d.part, part_off,
       last ? 1 : 0, part_total);
 }
 
-template <typename T, typename Y>
+template <typename T, typename Y, bool TMA>
 void fwd_any(const DeviceLayout &d, int c, const double *r, Y *y, bool check_done, cudaStream_t s,
              const WidePlan &p) {
   switch (wide_threads(d, c)) {
-    case 1024: fwd_nt<T, Y, 1024>(d, c, r, y, check_done, s, p); break;
-    case 512: fwd_nt<T, Y, 512>(d, c, r, y, check_done, s, p); break;
-    default: fwd_nt<T, Y, 256>(d, c, r, y, check_done, s, p); break;
+    case 1024: fwd_nt<T, Y, 1024, TMA>(d, c, r, y, check_done, s, p); break;
+    case 512: fwd_nt<T, Y, 512, TMA>(d, c, r, y, check_done, s, p); break;
+    default: fwd_nt<T, Y, 256, TMA>(d, c, r, y, check_done, s, p); break;
   }
 }
 
-template <typename T, typename Y>
+template <typename T, typename Y, bool TMA>
 void bwd_any(const DeviceLayout &d, int c, const Y *yin, const double *r, int dot_mode, bool check_done,
              int64_t part_off, bool last, int64_t part_total, cudaStream_t s, const WidePlan &p) {
   switch (wide_threads(d, c)) {
-    case 1024: bwd_nt<T, Y, 1024>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
-    case 512: bwd_nt<T, Y, 512>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
-    default: bwd_nt<T, Y, 256>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
+    case 1024: bwd_nt<T, Y, 1024, TMA>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
+    case 512: bwd_nt<T, Y, 512, TMA>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
+    default: bwd_nt<T, Y, 256, TMA>(d, c, yin, r, dot_mode, check_done, part_off, last, part_total, s, p); break;
   }
+}
+
+// Waves of CUDA blocks a color needs with a plan: level-1 blocks per SM over
+// the blocks an SM holds (by threads and by shared memory).
+static int64_t wide_waves(const DeviceLayout &d, int c, const WidePlan &p) {
+  const int64_t per_sm = (wide_color_grid(d, c) + d.sm_count - 1) / d.sm_count;
+  const int64_t by_threads = 2048 / wide_threads(d, c);
+  const int64_t by_smem = std::max<int64_t>(1, (int64_t)(227 * 1024) / ((int64_t)p.smem_bytes + 1024));
+  return (per_sm + std::min(by_threads, by_smem) - 1) / std::min(by_threads, by_smem);
+}
+
+// Bulk-copy staging saves trips to memory but holds the column run in shared
+// memory too, so fewer CUDA blocks share an SM.  Measured: it wins when a
+// color has at most two level-1 blocks per SM (27-point 96^3), loses with
+// five (3-DOF 100^3).  So: bulk copies when they need fewer waves, or as
+// many and the color has at most two level-1 blocks per SM.
+static bool wide_use_tma(const DeviceLayout &d, bool fwd, int prec, int c) {
+  const WidePlan &pt = wide_tma_plan(d, fwd, prec);
+  if (!pt.ok || d.sweep_kernel == 6) return false;
+  const int64_t wt = wide_waves(d, c, pt), wp = wide_waves(d, c, wide_plan(d, fwd, prec));
+  return wt < wp || (wt == wp && wide_color_grid(d, c) <= 2 * (int64_t)d.sm_count);
 }
 
 void launch_fwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done,
                            cudaStream_t s) {
   if (wide_color_grid(d, c) == 0) return;
-  const WidePlan &p = wide_plan(d, true, prec);
-  if (prec == HBMC_PREC_F64) fwd_any<double, double>(d, c, r, d.y, check_done, s, p);
-  else fwd_any<float, float>(d, c, r, d.y32, check_done, s, p);
+  const WidePlan &pt = wide_tma_plan(d, true, prec);
+  const bool tma = wide_use_tma(d, true, prec, c);
+  const WidePlan &p = tma ? pt : wide_plan(d, true, prec);
+  if (prec == HBMC_PREC_F64) {
+    if (tma) fwd_any<double, double, true>(d, c, r, d.y, check_done, s, p);
+    else fwd_any<double, double, false>(d, c, r, d.y, check_done, s, p);
+  } else {
+    if (tma) fwd_any<float, float, true>(d, c, r, d.y32, check_done, s, p);
+    else fwd_any<float, float, false>(d, c, r, d.y32, check_done, s, p);
+  }
 }
 
 void launch_bwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
                            int64_t part_off, bool last, int64_t part_total, cudaStream_t s) {
   if (wide_color_grid(d, c) == 0) return;
-  const WidePlan &p = wide_plan(d, false, prec);
-  if (prec == HBMC_PREC_F64) bwd_any<double, double>(d, c, d.y, r, dot_mode, check_done, part_off, last, part_total, s, p);
-  else bwd_any<float, float>(d, c, d.y32, r, dot_mode, check_done, part_off, last, part_total, s, p);
+  const WidePlan &pt = wide_tma_plan(d, false, prec);
+  const bool tma = wide_use_tma(d, false, prec, c);
+  const WidePlan &p = tma ? pt : wide_plan(d, false, prec);
+  if (prec == HBMC_PREC_F64) {
+    if (tma) bwd_any<double, double, true>(d, c, d.y, r, dot_mode, check_done, part_off, last, part_total, s, p);
+    else bwd_any<double, double, false>(d, c, d.y, r, dot_mode, check_done, part_off, last, part_total, s, p);
+  } else {
+    if (tma) bwd_any<float, float, true>(d, c, d.y32, r, dot_mode, check_done, part_off, last, part_total, s, p);
+    else bwd_any<float, float, false>(d, c, d.y32, r, dot_mode, check_done, part_off, last, part_total, s, p);
+  }
 }
 
 }  // namespace hbmc
