@@ -64,6 +64,7 @@ def _load():
                 "orc_spmv": (None, [I, P, P, P, P, P]),
                 "orc_dot": (D, [I, P, P, P, C]),
                 "orc_pcg": (C, [I, P, P, P, P, P, P, P, I, P, C, D, I, P, P, P]),
+                "orc_sor": (C, [I, P, P, P, P, P, D, I, C]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -182,6 +183,29 @@ def spmv(row_ptr, col, val, p):
     q = np.empty(len(rp) - 1)
     _load().orc_spmv(len(rp) - 1, _p(rp), _p(ci), _p(_f64(val)), _p(_f64(p)), _p(q))
     return q
+
+
+def sor(row_ptr, col, val, b, x0, omega=1.0, sweeps=1, symmetric=False):
+    """SOR (symmetric SOR when `symmetric`) sweeps on a CSR matrix in its own
+    index order, from x0; returns the new x (orc_sor: Section 2, Eq. "xj")."""
+    rp, ci = _i64(row_ptr), _i32(col)
+    x = _f64(x0).copy()
+    if _load().orc_sor(len(rp) - 1, _p(rp), _p(ci), _p(_f64(val)), _p(_f64(b)), _p(x), float(omega), int(sweeps),
+                       1 if symmetric else 0):
+        raise ValueError("a row has no nonzero diagonal entry")
+    return x
+
+
+def sor_solve(an, b, x0=None, omega=1.0, sweeps=1, symmetric=False):
+    """SOR sweeps on Abar with b and x0 in the original ordering; returns x in
+    the original ordering (dummy rows stay 0)."""
+    bbar = np.zeros(an.n_pad)
+    bbar[an.pi] = b
+    xbar = np.zeros(an.n_pad)
+    if x0 is not None:
+        xbar[an.pi] = x0
+    xbar = sor(an.row_ptr, an.col, an.val, bbar, xbar, omega, sweeps, symmetric)
+    return xbar[an.pi].copy()
 
 
 def dot(a, b, idx=None, mode=DOT_EXACT):

@@ -516,3 +516,43 @@ done:
   free(q);
   return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* SOR and symmetric SOR sweeps (Section 2: the iteration steps of the GS    */
+/* and SOR methods are substitutions like those of IC(0); Section 3.1, Eq.   */
+/* "xj": an equivalent reordering gives the same iterates).                  */
+/*                                                                          */
+/* On the reordered matrix, row by row in index order (forward sweep: i     */
+/* ascending; the backward sweep of symmetric SOR: i descending):           */
+/*   s   = sum_{j != i} abar_ij x_j    (ascending column, one fma per term,  */
+/*                                      starting from zero)                  */
+/*   t   = (b_i - s) / abar_ii                                               */
+/*   x_i = fma(omega, t - x_i, x_i)                                          */
+/* x is overwritten in place, so every x_j read is the newest value of row  */
+/* j.  omega = 1 is Gauss-Seidel.  Returns 0, or 1 if a row has no diagonal */
+/* entry or a zero one.                                                      */
+/* ------------------------------------------------------------------------ */
+static int sor_row(int64_t i, const int64_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
+                   double omega) {
+  double s = 0.0, d = 0.0;
+  for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+    if (ci[e] == i) d = v[e];
+    else s = fma(v[e], x[ci[e]], s);
+  }
+  if (d == 0.0) return 1;
+  const double t = (b[i] - s) / d;
+  x[i] = fma(omega, t - x[i], x[i]);
+  return 0;
+}
+
+ORC_API int orc_sor(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
+                    double omega, int64_t sweeps, int symmetric) {
+  for (int64_t k = 0; k < sweeps; ++k) {
+    for (int64_t i = 0; i < n; ++i)
+      if (sor_row(i, rp, ci, v, b, x, omega)) return 1;
+    if (symmetric)
+      for (int64_t i = n - 1; i >= 0; --i)
+        if (sor_row(i, rp, ci, v, b, x, omega)) return 1;
+  }
+  return 0;
+}
