@@ -275,6 +275,29 @@ hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev);
 hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
 
 /*
+ * hbmc_sor - SOR sweeps on the HBMC ordering (Section 2: the GS and SOR
+ * iteration steps are substitutions like IC(0)'s; Section 3.1, Eq. "xj":
+ * the equivalent reordering gives the same iterates, so each color's
+ * level-1 blocks run in parallel).  Row by row in the reordered order
+ * (forward sweep ascending; with symmetric != 0 every sweep is followed by a
+ * backward sweep, descending: symmetric SOR):
+ *   s = sum_{j != i} abar_ij x_j (ascending column, one fused multiply-add
+ *   per term from zero), t = (b_i - s) / abar_ii, x_i = fma(omega, t - x_i, x_i).
+ * omega = 1 is Gauss-Seidel.  b_dev, x_dev: device doubles of length n in the
+ * original ordering; x_dev holds the initial guess on entry and the result
+ * on exit.  omega in (0, 2), sweeps >= 0.  relres (host, may be NULL)
+ * receives ||b - A x|| / ||b|| after the sweeps (0 for b = 0).  Needs the
+ * context's level-1 block of SpMV entries to fit in shared memory (else
+ * HBMC_ERR_INVALID_ARG).  Does not need hbmc_ic0.  Synchronizes.
+ */
+hbmc_status hbmc_sor(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double omega, int32_t sweeps,
+                     int32_t symmetric, double *relres);
+/* The same on reordered vectors (length n_pad, HBMC order, dummies 0), with
+ * no permutation and no residual; asynchronous on the context's stream. */
+hbmc_status hbmc_sor_bar(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double omega, int32_t sweeps,
+                         int32_t symmetric);
+
+/*
  * hbmc_spmv_dot_static - q = Abar p and p.q without allocating anything.
  *
  * The paper has no counterpart: this exists for callers that cannot

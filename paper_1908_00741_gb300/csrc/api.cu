@@ -171,6 +171,8 @@ hbmc_status upload(hbmc_ctx *ctx) {
   CK(hbmc::setup_spmv_tma());
   hbmc::plan_wide_kernels(h, d);
   CK(hbmc::setup_wide_kernels());
+  hbmc::plan_sor(h, d);
+  CK(hbmc::setup_sor());
   if (d.sweep_kernel == 2) {
     std::vector<int32_t> rf, rb;
     hbmc::plan_tma(h, d.tma_f, d.tma_b, rf, rb);
@@ -625,6 +627,54 @@ hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev) {
   hbmc::enqueue_spmv(d, d.t, d.q, false, ctx->stream);
   CK(cudaMemcpyAsync(q_dev, d.q, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaGetLastError());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_sor_bar(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double omega, int32_t sweeps,
+                         int32_t symmetric) {
+  TRY(need_device(ctx));
+  if (!(omega > 0.0 && omega < 2.0) || sweeps < 0)
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "omega must be in (0, 2) and sweeps >= 0");
+  if (ctx->h.n == 0 || sweeps == 0) return HBMC_OK;
+  if (!b_dev || !x_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  if (!hbmc::sor_usable(d)) return set_err(ctx, HBMC_ERR_INVALID_ARG, "a level-1 block's rows do not fit in shared memory");
+  const size_t bytes = sizeof(double) * (size_t)d.n_pad;
+  CK(cudaMemcpyAsync(d.b, b_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d.x, x_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  hbmc::enqueue_sor(d, d.x, d.b, omega, sweeps, symmetric != 0, ctx->stream);
+  CK(cudaMemcpyAsync(x_dev, d.x, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaGetLastError());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_sor(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double omega, int32_t sweeps,
+                     int32_t symmetric, double *relres) {
+  if (relres) *relres = 0.0;
+  TRY(need_device(ctx));
+  if (!(omega > 0.0 && omega < 2.0) || sweeps < 0)
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "omega must be in (0, 2) and sweeps >= 0");
+  if (ctx->h.n == 0) return HBMC_OK;
+  if (!b_dev || !x_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  if (!hbmc::sor_usable(d)) return set_err(ctx, HBMC_ERR_INVALID_ARG, "a level-1 block's rows do not fit in shared memory");
+  Scalars init;
+  std::memset(&init, 0, sizeof init);
+  init.tol = 0.0;
+  init.bad_row = LLONG_MAX;
+  *ctx->h_sc = init;
+  CK(cudaMemcpyAsync(d.sc, ctx->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
+  hbmc::enqueue_gather_in(d, b_dev, d.b, 2, ctx->stream);
+  hbmc::enqueue_gather_in(d, x_dev, d.x, 2, ctx->stream);
+  hbmc::enqueue_sor(d, d.x, d.b, omega, sweeps, symmetric != 0, ctx->stream);
+  hbmc::enqueue_gather_out(d, d.x, x_dev, false, ctx->stream);
+  hbmc::enqueue_relres(d, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_sc, d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (relres) *relres = ctx->h_sc->relres;
   return HBMC_OK;
 }
 

@@ -143,6 +143,12 @@ struct WidePlan {
   bool ok = false;
 };
 
+// Shared memory of the SOR sweep kernel (sor.cu), byte offsets.
+struct SorPlan {
+  uint32_t off_xs = 0, off_bb = 0, off_sv = 0, off_gv = 0, off_tg = 0, smem_bytes = 0;
+  bool ok = false;
+};
+
 // Stage ring of the bulk-copy-fed SpMV (spmv_tma.cu); stages = 0: not used.
 struct SpmvPlan {
   int64_t nslices = 0, nchunks = 0;
@@ -182,6 +188,7 @@ struct DeviceLayout {
   WarpPlan wp_f64_f, wp_f64_b, wp_f32_f, wp_f32_b, wp_spmv;
   TwPlan tw_f64_f, tw_f64_b, tw_f32_f, tw_f32_b;
   SpmvPlan sp;
+  SorPlan sor;
   WidePlan wd_f64_f, wd_f64_b, wd_f32_f, wd_f32_b;  // plain-load staging
   WidePlan wt_f64_f, wt_f64_b, wt_f32_f, wt_f32_b;  // bulk-copy staging (w = 32)
   std::vector<uint8_t> wide_f, wide_b;  // per color: the loader-thread sweep is the faster one

@@ -669,6 +669,12 @@ void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode,
   }
 }
 
+// ||b - A x|| / ||b|| of the context's b and x into the scalars' relres.
+void enqueue_relres(const DeviceLayout &d, cudaStream_t s) {
+  k_residual<0><<<row_grid(d), kRowThreads, 0, s>>>(
+      d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, d.b, d.x, d.r, d.part, d.sc, d.hist);
+}
+
 // Before the loop: permute b and x0 in, r = b - A x, ||b||, z = M^{-1} r,
 // rho = r.z, p = z.
 void enqueue_init(const DeviceLayout &d, int prec, cudaStream_t s) {

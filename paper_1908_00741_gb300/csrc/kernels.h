@@ -53,6 +53,13 @@ bool spmv_tma_usable(const DeviceLayout &d);
 int64_t spmv_tma_partials_needed(const DeviceLayout &d);
 void enqueue_spmv_tma(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);
 
+// SOR / symmetric SOR sweeps on the HBMC ordering (sor.cu)
+void plan_sor(const HostLayout &h, DeviceLayout &d);
+cudaError_t setup_sor();
+bool sor_usable(const DeviceLayout &d);
+void enqueue_sor(const DeviceLayout &d, double *x, const double *b, double omega, int64_t sweeps, bool symmetric,
+                 cudaStream_t s);
+
 // TMA-fed substitution kernels (sweep_tma.cu)
 void plan_tma(const HostLayout &h, TmaPlan &pf, TmaPlan &pb, std::vector<int32_t> &rec_f,
               std::vector<int32_t> &rec_b);
@@ -73,6 +80,7 @@ void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode,
 void enqueue_init(const DeviceLayout &d, int prec, cudaStream_t s);
 void enqueue_body(const DeviceLayout &d, int prec, cudaStream_t s, bool use_cond, cudaGraphConditionalHandle h);
 void enqueue_final(const DeviceLayout &d, cudaStream_t s);
+void enqueue_relres(const DeviceLayout &d, cudaStream_t s);
 void enqueue_update_xr(const DeviceLayout &d, cudaStream_t s);
 void enqueue_update_p(const DeviceLayout &d, cudaStream_t s);
 void enqueue_ic0(const DeviceLayout &d, double shift, cudaStream_t s);

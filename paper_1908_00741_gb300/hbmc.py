@@ -45,7 +45,7 @@ EXPORTED = [
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
-    "hbmc_spmv_dot_static",
+    "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar",
     "hbmc_batch_build", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
     "hbmc_batch_set_stream", "hbmc_batch_set_precision", "hbmc_batch_ic0", "hbmc_batch_iccg",
     "hbmc_batch_autotune", "hbmc_batch_features",
@@ -119,6 +119,8 @@ def load():
             "hbmc_spmv_bar": (I32, [P, P, P]),
             "hbmc_profile_kernels": (I32, [P, I32, P]),
             "hbmc_spmv_dot_static": (I32, [P, P, P, P]),
+            "hbmc_sor": (I32, [P, P, P, D, I32, I32, P]),
+            "hbmc_sor_bar": (I32, [P, P, P, D, I32, I32]),
             "hbmc_batch_build": (I32, [I32, P, I32, P, P]),
             "hbmc_batch_destroy": (None, [P]),
             "hbmc_batch_last_error": (ctypes.c_char_p, [P]),
@@ -329,6 +331,23 @@ def hbmc_iccg_host(ctx: Context, b: np.ndarray, x: np.ndarray, tol=1e-8, maxit=1
                                 ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tr))
     ctx.check(s, (OK, NOT_CONVERGED, ERR_BREAKDOWN))
     return SolveResult(s, int(it.value), float(rr.value), float(tr.value))
+
+
+def hbmc_sor(ctx: Context, b, x, omega=1.0, sweeps=1, symmetric=False) -> float:
+    """SOR (symmetric SOR) sweeps on device tensors b, x of length n in the
+    original ordering (x: initial guess in, result out); returns
+    ||b - A x|| / ||b|| after the sweeps."""
+    rr = ctypes.c_double(0)
+    ctx.check(ctx._lib.hbmc_sor(ctx.handle, _dev_ptr(b, ctx.n, "b"), _dev_ptr(x, ctx.n, "x"), float(omega),
+                                int(sweeps), 1 if symmetric else 0, ctypes.byref(rr)))
+    return float(rr.value)
+
+
+def hbmc_sor_bar(ctx: Context, b, x, omega=1.0, sweeps=1, symmetric=False) -> None:
+    """The same on reordered device vectors of length n_pad (no residual)."""
+    n_pad = ctx.info()["n_pad"]
+    ctx.check(ctx._lib.hbmc_sor_bar(ctx.handle, _dev_ptr(b, n_pad, "b"), _dev_ptr(x, n_pad, "x"), float(omega),
+                                    int(sweeps), 1 if symmetric else 0))
 
 
 def hbmc_residual_history(ctx: Context, cap: int = 100000) -> np.ndarray:
