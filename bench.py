@@ -588,6 +588,85 @@ def run_orderings(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sor(args):
+    """Symmetric SOR (SSOR) sweeps on the 128^3 7-point workload, HBMC order
+    with bs = 8, w = 32 (the Gauss-Seidel/SOR use of the ordering, Section 2).
+    A step is hbmc_sor with `--sor-sweeps` symmetric sweeps (omega 1.5);
+    the metric is ms per symmetric sweep.  Algorithmic bytes of one
+    half-sweep: nnz * 12 (columns and values) + 3 n * 8 (x in, b in, x out)."""
+    import torch
+    from paper_1908_00741_gb300 import hbmc as H
+    from paper_1908_00741_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    P = W.poisson_problem(GRID, bs=DEFAULT_BS)
+    ctx = H.hbmc_build(P.A, DEFAULT_BS, 32, box=P.box, device=local)
+    stream = torch.cuda.current_stream()
+    H.hbmc_set_stream(ctx, stream)
+    b = torch.tensor(P.b, device="cuda")
+    x = torch.zeros_like(b)
+    sweeps, omega = args.sor_sweeps, 1.5
+    for _ in range(args.warmup):
+        x.zero_()
+        rel = H.hbmc_sor(ctx, b, x, omega, sweeps, True)
+    torch.cuda.synchronize()
+    barrier(dist)
+    with ClockSampler(local) as clk:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            x.zero_()
+            rel = H.hbmc_sor(ctx, b, x, omega, sweeps, True)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms_step = max_over_ranks(dist, ev[0].elapsed_time(ev[1]) / args.steps, "cuda")
+    # kernel-only: the sweeps alone on reordered vectors
+    n_pad = ctx.info()["n_pad"]
+    bb = torch.zeros(n_pad, dtype=torch.float64, device="cuda")
+    xb = torch.zeros_like(bb)
+    H.hbmc_sor_bar(ctx, bb, xb, omega, 2, True)
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    a.record(stream)
+    H.hbmc_sor_bar(ctx, bb, xb, omega, reps, True)
+    c.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = a.elapsed_time(c) / reps
+    half_bytes = P.A.nnz * 12 + 3 * P.A.n * 8
+    peak, peak_kind = measured_peaks()
+    gbs = 2 * half_bytes / (sweep_ms * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        an = oracle.analyse(P.A, DEFAULT_BS, 32, box=P.box)
+        t = time.perf_counter()
+        oracle.sor_solve(an, P.b, omega=omega, sweeps=2, symmetric=True)
+        dt = (time.perf_counter() - t) / 2
+        cpu = {"value": round(dt * 1e3, 3), "unit": "ms per symmetric sweep", "cores": 1, "kind": "oracle",
+               "sample": "2 symmetric sweeps of the 128^3 system (orc_sor, one core)"}
+    if rank != 0:
+        return
+    line = {
+        "metric": "symmetric SOR sweep time on the HBMC ordering", "value": round(sweep_ms, 4),
+        "unit": "ms per symmetric sweep", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"7-point Poisson {GRID}^3, bs={DEFAULT_BS} (2x2x2 boxes), w=32, omega {omega}, "
+                               f"{sweeps} symmetric sweeps per step", "n": P.A.n, "nnz": P.A.nnz},
+        "relres_after_step": rel,
+        "roofline": {"bound": "hbm", "kernel": "k_sor (both halves of a symmetric sweep)",
+                     "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                     "traffic": None, "algorithmic_bytes": 2 * half_bytes, "peak_source": peak_kind},
+        "e2e": {"value": round(ms_step, 4), "unit": "ms per step (permutations, sweeps, residual)",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "clocks": clk.summary(), "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -634,9 +713,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--bs", type=int, default=DEFAULT_BS)
-    ap.add_argument("--workload", default="poisson128", choices=["poisson128", "batch", "learned", "orderings"],
+    ap.add_argument("--workload", default="poisson128",
+                    choices=["poisson128", "batch", "learned", "orderings", "sor"],
                     help="poisson128: the headline solve; batch: 256 uneven systems solved together; "
-                         "learned: learned IC shift against the plain rule; orderings: MC, BMC and HBMC")
+                         "learned: learned IC shift against the plain rule; orderings: MC, BMC and HBMC; "
+                         "sor: symmetric SOR sweeps")
+    ap.add_argument("--sor-sweeps", type=int, default=10)
     ap.add_argument("--learned-train", type=int, default=200)
     ap.add_argument("--learned-heldout", type=int, default=40)
     ap.add_argument("--veclap-m", type=int, default=100)
@@ -659,7 +741,8 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build()
-        {"batch": run_batch, "learned": run_learned, "orderings": run_orderings}.get(args.workload, run_gpu)(args)
+        {"batch": run_batch, "learned": run_learned, "orderings": run_orderings,
+         "sor": run_sor}.get(args.workload, run_gpu)(args)
 
 
 if __name__ == "__main__":

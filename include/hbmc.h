@@ -282,7 +282,8 @@ hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
  * (forward sweep ascending; with symmetric != 0 every sweep is followed by a
  * backward sweep, descending: symmetric SOR):
  *   s = sum_{j != i} abar_ij x_j (ascending column, one fused multiply-add
- *   per term from zero), t = (b_i - s) / abar_ii, x_i = fma(omega, t - x_i, x_i).
+ *   per term from zero), t = (b_i - s) * (1 / abar_ii),
+ *   x_i = fma(omega, t - x_i, x_i).
  * omega = 1 is Gauss-Seidel.  b_dev, x_dev: device doubles of length n in the
  * original ordering; x_dev holds the initial guess on entry and the result
  * on exit.  omega in (0, 2), sweeps >= 0.  relres (host, may be NULL)

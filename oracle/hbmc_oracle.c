@@ -526,7 +526,8 @@ done:
 /* ascending; the backward sweep of symmetric SOR: i descending):           */
 /*   s   = sum_{j != i} abar_ij x_j    (ascending column, one fma per term,  */
 /*                                      starting from zero)                  */
-/*   t   = (b_i - s) / abar_ii                                               */
+/*   t   = (b_i - s) * dinv_i,  dinv_i = 1 / abar_ii (the reciprocal, as in  */
+/*                                      Fig. "C-vec"'s diaginv)               */
 /*   x_i = fma(omega, t - x_i, x_i)                                          */
 /* x is overwritten in place, so every x_j read is the newest value of row  */
 /* j.  omega = 1 is Gauss-Seidel.  Returns 0, or 1 if a row has no diagonal */
@@ -540,7 +541,7 @@ static int sor_row(int64_t i, const int64_t *rp, const int32_t *ci, const double
     else s = fma(v[e], x[ci[e]], s);
   }
   if (d == 0.0) return 1;
-  const double t = (b[i] - s) / d;
+  const double t = (b[i] - s) * (1.0 / d);
   x[i] = fma(omega, t - x[i], x[i]);
   return 0;
 }

@@ -145,7 +145,7 @@ struct WidePlan {
 
 // Shared memory of the SOR sweep kernel (sor.cu), byte offsets.
 struct SorPlan {
-  uint32_t off_xs = 0, off_bb = 0, off_sv = 0, off_gv = 0, off_tg = 0, smem_bytes = 0;
+  uint32_t off_cb = 0, off_bb = 0, off_dd = 0, off_sv = 0, off_ix = 0, smem_bytes = 0;
   bool ok = false;
 };
 

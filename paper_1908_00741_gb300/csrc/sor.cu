@@ -8,14 +8,14 @@
 // block per level-1 block:
 //   1. the level-1 block's x, b and slice offsets into shared memory;
 //   2. every thread takes a share of the block's SpMV entries (Section
-//      4.3.2's SELL rows of Abar, ascending columns): coefficient and a tag
-//      -- the step of a same-block column, or "other color" with the
-//      gathered x value (earlier colors already hold this sweep's values,
-//      later colors the previous ones);
+//      4.3.2's SELL rows of Abar, ascending columns): the coefficient, and
+//      where its x value will be -- a same-block row, or the gathered x of
+//      another color (earlier colors already hold this sweep's values, later
+//      colors the previous ones); the diagonal gives 1 / a_ii;
 //   3. lane j < w of the first warp runs BMC block j's chain of bs rows:
 //      s = sum_{col != i} a_ij x_j (ascending column, fma from zero, x_j of
 //      the same block from shared memory as the chain updates it),
-//      t = (b_i - s) / a_ii, x_i = fma(omega, t - x_i, x_i);
+//      t = (b_i - s) * (1 / a_ii), x_i = fma(omega, t - x_i, x_i);
 //   4. the rows of x are stored.
 // The operations and their order are the oracle's (orc_sor), so x is
 // bit-identical to it.
@@ -34,7 +34,6 @@ namespace {
 constexpr int kSorThreads = 256;
 constexpr int kSorU = 4;
 constexpr size_t kSorSmemBudget = 200 * 1024;
-constexpr uint8_t kOther = 255;
 
 struct SorArgs {
   const int64_t *a_ptr;
@@ -42,19 +41,26 @@ struct SorArgs {
   const double *a_val;
   int bs, w, lw;
   int64_t tile0;
-  uint32_t off_xs, off_bb, off_sv, off_gv, off_tg;
+  uint32_t off_cb, off_bb, off_dd, off_sv, off_ix;
 };
 
+// Shared memory of one level-1 block: rel[bs+1] slice offsets; cb = the
+// block's own x (R values, updated by the chains) followed by one gathered
+// x value per SpMV entry and a zero slot; bb = b; dd = 1 / a_ii; sv = the
+// entries' coefficients; ix = where in cb each entry's x value lives (a
+// same-block row, its own gathered slot, or the zero slot for the diagonal,
+// whose coefficient then adds nothing).  Every term is then one fma with no
+// branch.
 template <bool FWD>
 __global__ void __launch_bounds__(kSorThreads, 6)
     k_sor(const SorArgs a, double *x, const double *__restrict__ b, double omega) {
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *rel = reinterpret_cast<int32_t *>(smem);
-  double *xs = reinterpret_cast<double *>(smem + a.off_xs);
+  double *cb = reinterpret_cast<double *>(smem + a.off_cb);
   double *bb = reinterpret_cast<double *>(smem + a.off_bb);
+  double *dd = reinterpret_cast<double *>(smem + a.off_dd);
   double *sv = reinterpret_cast<double *>(smem + a.off_sv);
-  double *gv = reinterpret_cast<double *>(smem + a.off_gv);
-  uint8_t *tg = smem + a.off_tg;
+  int32_t *ix = reinterpret_cast<int32_t *>(smem + a.off_ix);
   const int tid = threadIdx.x;
   const int64_t u = a.tile0 + blockIdx.x;
   const int R = a.bs << a.lw;
@@ -64,9 +70,11 @@ __global__ void __launch_bounds__(kSorThreads, 6)
   // 1.
   for (int k = tid; k <= a.bs; k += kSorThreads) rel[k] = (int32_t)(a.a_ptr[s0 + k] - base);
   for (int lr = tid; lr < R; lr += kSorThreads) {
-    xs[lr] = x[row0 + lr];
+    cb[lr] = x[row0 + lr];
     bb[lr] = b[row0 + lr];
   }
+  if (tid == 0) cb[R + len] = 0.0;
+  __syncthreads();
   // 2.
   for (int e0 = tid; e0 < len; e0 += kSorThreads * kSorU) {
     int32_t c[kSorU];
@@ -87,13 +95,21 @@ __global__ void __launch_bounds__(kSorThreads, 6)
 #pragma unroll
     for (int k = 0; k < kSorU; ++k) {
       const int e = e0 + k * kSorThreads;
-      if (e < len) {
-        sv[e] = v[k];
-        if (c[k] < row0 || c[k] >= row0 + R) {
-          tg[e] = kOther;
-          gv[e] = g[k];
+      if (e >= len) continue;
+      sv[e] = v[k];
+      if (c[k] < row0 || c[k] >= row0 + R) {
+        cb[R + e] = g[k];
+        ix[e] = R + e;
+      } else {
+        // inside the level-1 block only lane j's own BMC block couples
+        const int off = (int)(c[k] - row0);
+        int l = 0;
+        while (e >= rel[l + 1]) ++l;  // the entry's own step
+        if ((off >> a.lw) == l) {
+          ix[e] = R + len;  // the diagonal: zero slot
+          dd[off] = 1.0 / v[k];
         } else {
-          tg[e] = (uint8_t)((c[k] - row0) >> a.lw);  // the coloring leaves only lane j's own block here
+          ix[e] = off;
         }
       }
     }
@@ -104,22 +120,18 @@ __global__ void __launch_bounds__(kSorThreads, 6)
     const int j = tid;
     for (int q = 0; q < a.bs; ++q) {
       const int l = FWD ? q : a.bs - 1 - q;
-      double s = 0.0, d = 0.0;
+      double s = 0.0;
       const int pe = rel[l + 1];
-      for (int p = rel[l] + j; p < pe; p += a.w) {
-        const int m = tg[p];
-        if (m == kOther) s = fma(sv[p], gv[p], s);
-        else if (m == l) d = sv[p];
-        else s = fma(sv[p], xs[(m << a.lw) + j], s);
-      }
+      for (int p = rel[l] + j; p < pe; p += a.w) s = fma(sv[p], cb[ix[p]], s);
       const int lr = (l << a.lw) + j;
-      const double t = (bb[lr] - s) / d;
-      xs[lr] = fma(omega, t - xs[lr], xs[lr]);
+      // explicit roundings: no multiply-subtract contraction across t
+      const double t = __dmul_rn(__dsub_rn(bb[lr], s), dd[lr]);
+      cb[lr] = fma(omega, __dsub_rn(t, cb[lr]), cb[lr]);
     }
   }
   __syncthreads();
   // 4.
-  for (int lr = tid; lr < R; lr += kSorThreads) x[row0 + lr] = xs[lr];
+  for (int lr = tid; lr < R; lr += kSorThreads) x[row0 + lr] = cb[lr];
 }
 
 uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
@@ -134,13 +146,13 @@ cudaError_t allow(K kernel) {
 void plan_sor(const HostLayout &h, DeviceLayout &d) {
   SorPlan &p = d.sor;
   p = SorPlan();
-  const uint64_t R = (uint64_t)h.bs * h.w;
-  p.off_xs = a16((uint64_t)(h.bs + 1) * 4);
-  p.off_bb = a16(p.off_xs + R * 8);
-  p.off_sv = a16(p.off_bb + R * 8);
-  p.off_gv = a16(p.off_sv + (uint64_t)h.max_a * 8);
-  p.off_tg = a16(p.off_gv + (uint64_t)h.max_a * 8);
-  const uint64_t total = a16(p.off_tg + (uint64_t)h.max_a);
+  const uint64_t R = (uint64_t)h.bs * h.w, E = (uint64_t)h.max_a;
+  p.off_cb = a16((uint64_t)(h.bs + 1) * 4);
+  p.off_bb = a16(p.off_cb + (R + E + 1) * 8);
+  p.off_dd = a16(p.off_bb + R * 8);
+  p.off_sv = a16(p.off_dd + R * 8);
+  p.off_ix = a16(p.off_sv + E * 8);
+  const uint64_t total = a16(p.off_ix + E * 4);
   p.smem_bytes = (uint32_t)std::min<uint64_t>(total, 0xffffffffu);
   p.ok = total <= kSorSmemBudget && h.bs <= 64;
 }
@@ -162,11 +174,11 @@ void enqueue_sor(const DeviceLayout &d, double *x, const double *b, double omega
   a.bs = d.bs;
   a.w = d.w;
   a.lw = d.lw;
-  a.off_xs = d.sor.off_xs;
+  a.off_cb = d.sor.off_cb;
   a.off_bb = d.sor.off_bb;
+  a.off_dd = d.sor.off_dd;
   a.off_sv = d.sor.off_sv;
-  a.off_gv = d.sor.off_gv;
-  a.off_tg = d.sor.off_tg;
+  a.off_ix = d.sor.off_ix;
   for (int64_t k = 0; k < sweeps; ++k) {
     for (int c = 0; c < d.nc; ++c) {
       a.tile0 = d.tile_ptr[c];
