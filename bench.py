@@ -295,6 +295,26 @@ def run_gpu(args):
 
     variants = {}
     if not args.no_variants:
+        # the 32^3 configuration (32,768 unknowns, bs 8, FP64): it sits in L2, so time only
+        P1 = W.poisson_problem(32, bs=8)
+        c1 = H.hbmc_build(P1.A, 8, 32, box=P1.box, device=local)
+        H.hbmc_set_stream(c1, stream)
+        H.hbmc_ic0(c1)
+        b1 = torch.tensor(P1.b, device="cuda")
+        x1 = torch.zeros_like(b1)
+        for _ in range(3):
+            x1.zero_()
+            r1 = H.hbmc_iccg(c1, b1, x1, tol=TOL)
+        a1, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a1.record(stream)
+        for _ in range(10):
+            x1.zero_()
+            r1 = H.hbmc_iccg(c1, b1, x1, tol=TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        variants["poisson32_bs8_f64"] = {"ms": round(a1.elapsed_time(e1) / 10, 3), "iters": r1.iters,
+                                         "true_relres": r1.true_relres}
+        c1.close()
         for vbs in (8, 16, 32):
             for vp in ("f64", "f32"):
                 if vbs == bs and vp == args.precision:
