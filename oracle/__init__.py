@@ -65,6 +65,9 @@ def _load():
                 "orc_dot": (D, [I, P, P, P, C]),
                 "orc_pcg": (C, [I, P, P, P, P, P, P, P, I, P, C, D, I, P, P, P]),
                 "orc_sor": (C, [I, P, P, P, P, P, D, I, C]),
+                "orc_ilu0": (I, [I, P, P, P, P, D, P, P, P, P]),
+                "orc_bwd_u": (None, [I, P, P, P, P, P, P]),
+                "orc_bicgstab": (C, [I, P, P, P, P, P, P, P, P, I, P, C, D, I, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -206,6 +209,51 @@ def sor_solve(an, b, x0=None, omega=1.0, sweeps=1, symmetric=False):
         xbar[an.pi] = x0
     xbar = sor(an.row_ptr, an.col, an.val, bbar, xbar, omega, sweeps, symmetric)
     return xbar[an.pi].copy()
+
+
+def ilu0(row_ptr, col, val, shift=0.0, tpos=None):
+    """ILU(0) of a CSR matrix with a symmetric pattern (orc_ilu0): returns
+    (lval, uval, udiag, uinv, bad_row) with lval / uval at the positions of
+    the strict lower / upper entries."""
+    rp, ci, v = _i64(row_ptr), _i32(col), _f64(val)
+    if tpos is None:
+        tpos = transpose_pos(rp, ci)
+    n = len(rp) - 1
+    lval, uval = np.zeros(len(ci)), np.zeros(len(ci))
+    udiag, uinv = np.zeros(n), np.zeros(n)
+    bad = _load().orc_ilu0(n, _p(rp), _p(ci), _p(v), _p(_i64(tpos)), float(shift), _p(lval), _p(uval),
+                           _p(udiag), _p(uinv))
+    return lval, uval, udiag, uinv, int(bad)
+
+
+def bwd_u(row_ptr, col, uval, uinv, y):
+    rp, ci = _i64(row_ptr), _i32(col)
+    z = np.empty(len(rp) - 1)
+    _load().orc_bwd_u(len(rp) - 1, _p(rp), _p(ci), _p(_f64(uval)), _p(_f64(uinv)), _p(_f64(y)), _p(z))
+    return z
+
+
+def factor_ilu(an, shift=0.0):
+    return ilu0(an.row_ptr, an.col, an.val, shift)
+
+
+def bicgstab(an, lval, uval, uinv, b, tol=1e-8, maxit=10000, x0=None, dot_mode=DOT_SEQUENTIAL):
+    """ILU(0)-preconditioned BiCGStab on Abar (orc_bicgstab); b and x0 in the
+    original ordering.  status: 0 converged, 1 maxit, 2 breakdown."""
+    bbar = np.zeros(an.n_pad)
+    bbar[an.pi] = b
+    xbar = np.zeros(an.n_pad)
+    if x0 is not None:
+        xbar[an.pi] = x0
+    hist = np.zeros(maxit + 1)
+    iters = ctypes.c_int64(0)
+    relres = ctypes.c_double(0.0)
+    order = _i64(an.pi)
+    st = _load().orc_bicgstab(an.n_pad, _p(an.row_ptr), _p(an.col), _p(an.val), _p(_f64(lval)), _p(_f64(uval)),
+                              _p(_f64(uinv)), _p(bbar), _p(xbar), len(order), _p(order), int(dot_mode), float(tol),
+                              int(maxit), ctypes.byref(iters), ctypes.byref(relres), _p(hist))
+    return Solve(xbar[an.pi].copy(), int(iters.value), float(relres.value), int(st),
+                 hist[: iters.value + 1].copy(), -1, xbar)
 
 
 def dot(a, b, idx=None, mode=DOT_EXACT):

@@ -557,3 +557,203 @@ ORC_API int orc_sor(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* ILU(0) and preconditioned BiCGStab for a nonsymmetric Abar whose pattern */
+/* is symmetric (Section 2: IC(0)/ILU(0) preconditioning; the HBMC ordering  */
+/* applies to ILU(0)'s substitutions as to IC(0)'s).                        */
+/* ------------------------------------------------------------------------ */
+
+/* ILU(0): Abar ~= L U, L unit lower with the pattern of the strict lower
+ * triangle, U upper with the pattern of the upper triangle (diagonal scaled
+ * by 1 + shift).  Row by row in index order, the row's entries in ascending
+ * column j:
+ *   w   = abar_ij - sum_{k < min(i,j)} l_ik u_kj   (k ascending, k in the row's
+ *          pattern and in column j's; one fma per term)
+ *   l_ij = w / u_jj  for j < i;   u_ij = w  for j >= i.
+ * lval / uval get l_ij / u_ij at the position of abar_ij (0 elsewhere); udiag
+ * gets u_ii and uinv 1 / u_ii.  tpos from orc_transpose_pos.  Returns -1, or
+ * the first row whose pivot u_ii is zero or not finite (it stops there). */
+ORC_API int64_t orc_ilu0(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const int64_t *tpos,
+                         double shift, double *lval, double *uval, double *udiag, double *uinv) {
+  const double scale = 1.0 + shift;
+  for (int64_t e = 0; e < rp[n]; ++e) {
+    lval[e] = 0.0;
+    uval[e] = 0.0;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int have_diag = 0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int64_t j = ci[e];
+      const int64_t lim = j < i ? j : i;
+      double s = j == i ? scale * v[e] : v[e];
+      /* k < lim in row i and in row j (pattern symmetry: (k, j) in the
+       * pattern iff k is a column of row j); u_kj sits at tpos of (j, k) */
+      int64_t p = rp[i], q = rp[j];
+      while (p < rp[i + 1] && ci[p] < lim && q < rp[j + 1] && ci[q] < lim) {
+        if (ci[p] == ci[q]) {
+          s = fma(-lval[p], uval[tpos[q]], s);
+          ++p;
+          ++q;
+        } else if (ci[p] < ci[q]) {
+          ++p;
+        } else {
+          ++q;
+        }
+      }
+      if (j < i) {
+        lval[e] = s / udiag[j];
+      } else if (j == i) {
+        if (s == 0.0 || !isfinite(s)) return i;
+        udiag[i] = s;
+        uinv[i] = 1.0 / s;
+        have_diag = 1;
+      } else {
+        uval[e] = s;
+      }
+    }
+    if (!have_diag) return i;
+  }
+  return -1;
+}
+
+/* Backward substitution with U: z_i = (y_i - sum_{j>i} u_ij z_j) * uinv_i,
+ * terms in descending j (farthest column first, as for IC(0)). */
+ORC_API void orc_bwd_u(int64_t n, const int64_t *rp, const int32_t *ci, const double *uval, const double *uinv,
+                       const double *y, double *z) {
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int64_t e = rp[i + 1] - 1; e >= rp[i] && ci[e] > i; --e) s = fma(-uval[e], z[ci[e]], s);
+    z[i] = s * uinv[i];
+  }
+}
+
+/* z = (L U)^{-1} r: unit-lower forward substitution (orc_fwd with all-ones
+ * dinv: y_i = (r_i - sum l_ij y_j) * 1), then orc_bwd_u. */
+static void ilu_apply(int64_t n, const int64_t *rp, const int32_t *ci, const double *lval, const double *ones,
+                      const double *uval, const double *uinv, const double *r, double *y, double *z) {
+  orc_fwd(n, rp, ci, lval, ones, r, y);
+  orc_bwd_u(n, rp, ci, uval, uinv, y, z);
+}
+
+/* Right-preconditioned BiCGStab (van der Vorst) on Abar with M = L U:
+ *   r = b - A x, rh = r, rho_old = alpha = omega = 1, p = v = 0, rho = (rh, r)
+ *   per iteration k:
+ *     beta = (rho / rho_old) * (alpha / omega)
+ *     p = r + beta (p - omega v)      [p_i = fma(beta, fma(-omega, v_i, p_i), r_i)]
+ *     ph = M^{-1} p,  v = A ph,  alpha = rho / (rh, v)
+ *     s = r - alpha v                 [fma(-alpha, v_i, r_i)]
+ *     if ||s|| / ||b|| < tol: x = x + alpha ph [fma], stop (iteration k counted)
+ *     sh = M^{-1} s,  t = A sh,  omega = (t, s) / (t, t)
+ *     x = x + alpha ph + omega sh     [fma(omega, sh_i, fma(alpha, ph_i, x_i))]
+ *     r = s - omega t                 [fma(-omega, t_i, s_i)]
+ *     stop when ||r|| / ||b|| < tol (iteration k counted)
+ *     rho_old = rho, rho = (rh, r)
+ * Dots as in orc_pcg.  Returns 0 converged, 1 maxit, 2 breakdown (rho,
+ * (rh, v), (t, t) or omega zero or not finite). */
+ORC_API int orc_bicgstab(int64_t n_pad, const int64_t *rp, const int32_t *ci, const double *v, const double *lval,
+                         const double *uval, const double *uinv, const double *b, double *x, int64_t m,
+                         const int64_t *order, int dot_mode, double tol, int64_t maxit, int64_t *iters_out,
+                         double *relres, double *hist) {
+  double *r = calloc(n_pad, sizeof(double)), *rh = calloc(n_pad, sizeof(double));
+  double *p = calloc(n_pad, sizeof(double)), *vv = calloc(n_pad, sizeof(double));
+  double *s = calloc(n_pad, sizeof(double)), *t = calloc(n_pad, sizeof(double));
+  double *ph = calloc(n_pad, sizeof(double)), *sh = calloc(n_pad, sizeof(double));
+  double *y = calloc(n_pad, sizeof(double)), *ones = calloc(n_pad, sizeof(double));
+  int status = 1;
+  int64_t k = 0;
+  for (int64_t i = 0; i < n_pad; ++i) ones[i] = 1.0;
+  orc_spmv(n_pad, rp, ci, v, x, t);
+  for (int64_t i = 0; i < n_pad; ++i) {
+    r[i] = b[i] - t[i];
+    rh[i] = r[i];
+  }
+  const double bnorm = sqrt(orc_dot(m, order, b, b, dot_mode));
+  if (bnorm == 0.0) {
+    for (int64_t i = 0; i < n_pad; ++i) x[i] = 0.0;
+    *relres = 0.0;
+    if (hist) hist[0] = 0.0;
+    status = 0;
+    goto done;
+  }
+  double res = sqrt(orc_dot(m, order, r, r, dot_mode)) / bnorm;
+  if (hist) hist[0] = res;
+  *relres = res;
+  if (res < tol) {
+    status = 0;
+    goto done;
+  }
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  double rho = orc_dot(m, order, rh, r, dot_mode);
+  for (k = 1; k <= maxit; ++k) {
+    if (rho == 0.0 || !isfinite(rho)) {
+      status = 2;
+      --k;
+      break;
+    }
+    const double beta = (rho / rho_old) * (alpha / omega);
+    for (int64_t i = 0; i < n_pad; ++i) p[i] = fma(beta, fma(-omega, vv[i], p[i]), r[i]);
+    ilu_apply(n_pad, rp, ci, lval, ones, uval, uinv, p, y, ph);
+    orc_spmv(n_pad, rp, ci, v, ph, vv);
+    const double rv = orc_dot(m, order, rh, vv, dot_mode);
+    if (rv == 0.0 || !isfinite(rv)) {
+      status = 2;
+      --k;
+      break;
+    }
+    alpha = rho / rv;
+    for (int64_t i = 0; i < n_pad; ++i) s[i] = fma(-alpha, vv[i], r[i]);
+    const double sres = sqrt(orc_dot(m, order, s, s, dot_mode)) / bnorm;
+    if (sres < tol) { /* the half step already meets the tolerance */
+      for (int64_t i = 0; i < n_pad; ++i) {
+        x[i] = fma(alpha, ph[i], x[i]);
+        r[i] = s[i];
+      }
+      if (hist) hist[k] = sres;
+      *relres = sres;
+      status = 0;
+      break;
+    }
+    ilu_apply(n_pad, rp, ci, lval, ones, uval, uinv, s, y, sh);
+    orc_spmv(n_pad, rp, ci, v, sh, t);
+    const double tt = orc_dot(m, order, t, t, dot_mode);
+    const double ts = orc_dot(m, order, t, s, dot_mode);
+    if (!(tt > 0.0) || !isfinite(tt)) {
+      status = 2;
+      --k;
+      break;
+    }
+    omega = ts / tt;
+    for (int64_t i = 0; i < n_pad; ++i) {
+      x[i] = fma(omega, sh[i], fma(alpha, ph[i], x[i]));
+      r[i] = fma(-omega, t[i], s[i]);
+    }
+    res = sqrt(orc_dot(m, order, r, r, dot_mode)) / bnorm;
+    if (hist) hist[k] = res;
+    *relres = res;
+    if (res < tol) {
+      status = 0;
+      break;
+    }
+    if (omega == 0.0 || !isfinite(omega)) {
+      status = 2;
+      break;
+    }
+    rho_old = rho;
+    rho = orc_dot(m, order, rh, r, dot_mode);
+  }
+  if (k > maxit) k = maxit;
+done:
+  *iters_out = k;
+  free(r);
+  free(rh);
+  free(p);
+  free(vv);
+  free(s);
+  free(t);
+  free(ph);
+  free(sh);
+  free(y);
+  free(ones);
+  return status;
+}

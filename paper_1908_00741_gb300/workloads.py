@@ -168,6 +168,29 @@ def heterogeneous_stencil(m: int, points: int, sigma: float, seed: int) -> CSR:
     return _grid_stencil(m, m, m, points, kappa)
 
 
+def convection_diffusion(m: int, velocity=(0.5, 0.3, 0.2)) -> CSR:
+    """Nonsymmetric 7-point convection-diffusion on m^3 (natural order, x
+    fastest, Dirichlet): -Laplace(u) + c . grad(u) with first-order upwind
+    differences for c >= 0 (grid units): the neighbour at -e_d gets
+    -(1 + c_d), the one at +e_d gets -1, the diagonal 6 + sum_d c_d.  The
+    pattern is symmetric, the values are not; an irreducibly diagonally
+    dominant M-matrix."""
+    n = m ** 3
+    idx = np.arange(n, dtype=np.int64)
+    x, y, z = idx % m, (idx // m) % m, idx // (m * m)
+    rows, cols, vals = [idx], [idx], [np.full(n, 6.0 + float(sum(velocity)))]
+    for d, (dz, dy, dx) in enumerate([(0, 0, 1), (0, 1, 0), (1, 0, 0)]):
+        c = float(velocity[d])  # d = 0: x, 1: y, 2: z
+        for sgn in (-1, 1):
+            xx, yy, zz = x + sgn * dx, y + sgn * dy, z + sgn * dz
+            inside = (xx >= 0) & (xx < m) & (yy >= 0) & (yy < m) & (zz >= 0) & (zz < m)
+            j = xx + m * (yy + m * zz)
+            rows.append(idx[inside])
+            cols.append(j[inside])
+            vals.append(np.full(int(inside.sum()), -(1.0 + c) if sgn < 0 else -1.0))
+    return _assemble(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), grid=(m, m, m))
+
+
 def permute_input(A: CSR, order: np.ndarray) -> CSR:
     """Relabel unknowns: input row k is natural row order[k] (A_in = Q A Q^T)."""
     n = A.n
@@ -286,6 +309,14 @@ def vector_laplacian_problem(m: int, bs: int = 8, w: int = 32, seed: int = 3,
     A = permute_input(A, random_order(order_seed, A.n))
     b, xs = rhs_from_solution(A, rhs_seed)
     return Problem(f"veclap_{m}^3_bs{bs}", A, b, xs, bs, w, None)
+
+
+def convection_diffusion_problem(m: int, bs: int = 8, w: int = 32, velocity=(0.5, 0.3, 0.2),
+                                 seed: int = 0) -> Problem:
+    """Nonsymmetric convection-diffusion on m^3, geometric bs-cubes, b = A x*."""
+    A = convection_diffusion(m, velocity)
+    b, xs = rhs_from_solution(A, seed)
+    return Problem(f"convdiff_{m}^3_bs{bs}", A, b, xs, bs, w, box_for_bs(bs))
 
 
 def batch_problems(nsys: int = 256, seed0: int = 1000, nmin: int = 16, nmax: int = 64):
