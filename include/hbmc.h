@@ -99,6 +99,8 @@ typedef struct hbmc_options {
                            SpMV (w = 32) is fed by bulk copies when a chunk of its slices fits
                            in shared memory, else one thread per row; with 3 it runs one warp
                            per level-1 block. */
+  int32_t nonsymmetric; /* 0: A must be symmetric (IC(0), CG); 1: only the pattern must be
+                           symmetric and the diagonal nonzero (ILU(0), BiCGStab) */
 } hbmc_options;
 
 /* Fills *opt with the defaults. */
@@ -273,6 +275,43 @@ hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev);
  * Synchronizes the stream.
  */
 hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
+
+/*
+ * hbmc_ilu0 - ILU(0) of Abar for a context built with opt.nonsymmetric = 1
+ * (Section 2: ILU(0) preconditioning; the HBMC ordering makes its
+ * substitutions parallel exactly as for IC(0), with U in place of L^T).
+ * Abar ~= L U, L unit lower triangular on the pattern of Abar's strict lower
+ * triangle, U upper triangular on the pattern of its upper triangle; the
+ * diagonal is scaled by (1 + shift).  Row by row in index order, entries in
+ * ascending column: w = abar_ij - sum_{k<min(i,j)} l_ik u_kj (one fma per
+ * term, k ascending), l_ij = w / u_jj for j < i, u_ij = w for j >= i.
+ * Computed color by color on the device (lane = BMC block, as hbmc_ic0).
+ * bad_row (may be NULL) gets -1 or the original index of the first row whose
+ * pivot u_ii is zero or not finite (status HBMC_ERR_NOT_SPD_PIVOT).
+ * hbmc_ic0 is refused on such a context, hbmc_ilu0 on a symmetric one.
+ * Synchronizes.
+ */
+hbmc_status hbmc_ilu0(hbmc_ctx *ctx, double shift, int64_t *bad_row);
+
+/* U of the ILU(0) factor on the positions of Abar's strict upper triangle
+ * (host double[nnz of Abar], as hbmc_get_matrix's values; zero elsewhere).
+ * hbmc_get_factor returns L and, for an ILU(0) context, the pivots u_ii. */
+hbmc_status hbmc_get_factor_u(const hbmc_ctx *ctx, double *upper);
+
+/*
+ * hbmc_bicgstab - ILU(0)-preconditioned BiCGStab (right preconditioning,
+ * van der Vorst) on Abar for a context built with opt.nonsymmetric = 1 and
+ * factored by hbmc_ilu0.  Per iteration: beta = (rho / rho_old)(alpha /
+ * omega), p = r + beta (p - omega v), ph = M^{-1} p, v = A ph, alpha = rho /
+ * (rh, v), s = r - alpha v (if ||s|| / ||b|| < tol: x += alpha ph and stop),
+ * sh = M^{-1} s, t = A sh, omega = (t, s) / (t, t), x += alpha ph + omega sh,
+ * r = s - omega t, stop when ||r|| / ||b|| < tol, rho_old = rho, rho = (rh,
+ * r); rh = r0.  Vectors, outputs and statuses as hbmc_iccg (HBMC_ERR_BREAKDOWN
+ * when rho, (rh, v), (t, t) or omega is zero or not finite).  Honours
+ * hbmc_set_precision (FP32 substitutions) and opt.loop_mode.  Synchronizes.
+ */
+hbmc_status hbmc_bicgstab(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double tol, int64_t maxit,
+                          int64_t *iters, double *relres, double *true_relres);
 
 /*
  * hbmc_sor - SOR sweeps on the HBMC ordering (Section 2: the GS and SOR

@@ -29,11 +29,14 @@ struct hbmc_ctx {
   int device = 0;
   bool host_only = false;
   bool factored = false;
+  int factor_kind = 0;  // 1 IC(0), 2 ILU(0)
   int32_t precision = HBMC_PREC_F64;
   cudaStream_t stream = nullptr;     // user stream (nullptr = legacy default)
   cudaStream_t cap[2] = {nullptr, nullptr};  // private streams used for graph capture
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraph_t bgraph[2] = {nullptr, nullptr};  // BiCGStab solve graphs per precision
+  cudaGraphExec_t bexec[2] = {nullptr, nullptr};
   Scalars *h_sc = nullptr;           // page-locked mirror of the device scalars
   double *stage_b = nullptr, *stage_x = nullptr;  // device staging for hbmc_iccg_host
   std::vector<void *> allocs;
@@ -134,6 +137,19 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dalloc(ctx, d.bi_val32, h.bi_m.size()));
   TRY(dalloc(ctx, d.dinv, h.n_pad));
   TRY(dalloc(ctx, d.dinv32, h.n_pad));
+  d.dinvb = d.dinv;
+  d.dinvb32 = d.dinv32;
+  d.nonsym = h.nonsym ? 1 : 0;
+  if (h.nonsym) {
+    TRY(dalloc(ctx, d.dinvb, h.n_pad));
+    TRY(dalloc(ctx, d.dinvb32, h.n_pad));
+    TRY(dupload(ctx, d.uaval, h.uaval));
+    TRY(dupload(ctx, d.urp, h.urp));
+    TRY(dupload(ctx, d.uci, h.uci));
+    TRY(dupload(ctx, d.upos, h.upos));
+    TRY(dalloc(ctx, d.uval, h.nnz_lower));
+    TRY(dalloc(ctx, d.udiag, h.n_pad));
+  }
   TRY(dupload(ctx, d.lrp, h.lrp));
   TRY(dupload(ctx, d.lci, h.lci));
   TRY(dupload(ctx, d.laval, h.laval));
@@ -153,6 +169,11 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dalloc(ctx, d.t, nv));
   TRY(dalloc(ctx, d.y32, nv));
   TRY(dalloc(ctx, d.z32, nv));
+  if (h.nonsym) {
+    TRY(dalloc(ctx, d.rh, nv));
+    TRY(dalloc(ctx, d.sv, nv));
+    TRY(dalloc(ctx, d.ph, nv));
+  }
   CK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
   while ((1 << d.lw) < d.w) ++d.lw;
   hbmc::sweep_geometry(h, d, ctx->opt.sweep_tpb);
@@ -204,16 +225,17 @@ hbmc_status need_device(hbmc_ctx *ctx) {
 // Capture the whole solve as one graph: init, a while node running one CG
 // iteration per pass (its condition is cleared on the device when the solve
 // is done), then the permutation out and the true residual.
-hbmc_status build_graph(hbmc_ctx *ctx, int prec) {
+hbmc_status build_graph(hbmc_ctx *ctx, int prec, bool bicg) {
   const DeviceLayout &d = ctx->d;
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
-  ctx->graph[prec] = g;
+  (bicg ? ctx->bgraph : ctx->graph)[prec] = g;
   cudaGraphConditionalHandle handle;
   CK(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
   cudaStream_t s = ctx->cap[0], s2 = ctx->cap[1];
   CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  hbmc::enqueue_init(d, prec, s);
+  if (bicg) hbmc::enqueue_bcg_init(d, s);
+  else hbmc::enqueue_init(d, prec, s);
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t *deps = nullptr;
   size_t ndeps = 0;
@@ -239,8 +261,11 @@ hbmc_status build_graph(hbmc_ctx *ctx, int prec) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    hbmc::enqueue_body(d, prec, s2, true, handle);
+    cudaError_t eb = cudaSuccess;
+    if (bicg) eb = hbmc::enqueue_bcg_body(d, prec, s2, true, handle);
+    else hbmc::enqueue_body(d, prec, s2, true, handle);
     e = cudaStreamEndCapture(s2, &body);
+    if (e == cudaSuccess) e = eb;
   }
   if (e != cudaSuccess) {
     cudaGraph_t junk;
@@ -250,12 +275,12 @@ hbmc_status build_graph(hbmc_ctx *ctx, int prec) {
   hbmc::enqueue_final(d, s);
   CK(cudaStreamEndCapture(s, &g));
   CK(cudaGetLastError());
-  CK(cudaGraphInstantiate(&ctx->exec[prec], g, 0));
+  CK(cudaGraphInstantiate(&(bicg ? ctx->bexec : ctx->exec)[prec], g, 0));
   return HBMC_OK;
 }
 
 hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double tol, int64_t maxit,
-                      int64_t *iters, double *relres, double *true_relres) {
+                      int64_t *iters, double *relres, double *true_relres, bool bicg = false) {
   if (iters) *iters = 0;
   if (relres) *relres = 0.0;
   if (true_relres) *true_relres = 0.0;
@@ -265,7 +290,9 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
     return HBMC_OK;
   }
   if (!b_dev || !x_dev) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null vector");
-  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "hbmc_ic0 has not succeeded on this context");
+  if (!ctx->factored) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "no factorization has succeeded on this context");
+  if (!bicg && ctx->factor_kind != 1)
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "CG needs the IC(0) factor of a symmetric matrix: use hbmc_bicgstab");
   const int prec = ctx->precision;
   const DeviceLayout &d = ctx->d;
   Scalars init;
@@ -278,13 +305,18 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
   *ctx->h_sc = init;
   CK(cudaMemcpyAsync(d.sc, ctx->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
   if (ctx->opt.loop_mode == HBMC_LOOP_GRAPH) {
-    if (!ctx->exec[prec]) TRY(build_graph(ctx, prec));
-    CK(cudaGraphLaunch(ctx->exec[prec], ctx->stream));
+    cudaGraphExec_t *ex = bicg ? ctx->bexec : ctx->exec;
+    if (!ex[prec]) TRY(build_graph(ctx, prec, bicg));
+    CK(cudaGraphLaunch(ex[prec], ctx->stream));
   } else {
-    hbmc::enqueue_init(d, prec, ctx->stream);
+    if (bicg) hbmc::enqueue_bcg_init(d, ctx->stream);
+    else hbmc::enqueue_init(d, prec, ctx->stream);
     const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
     for (int64_t k = 0;; k += every) {
-      for (int t = 0; t < every; ++t) hbmc::enqueue_body(d, prec, ctx->stream, false, 0);
+      for (int t = 0; t < every; ++t) {
+        if (bicg) CK(hbmc::enqueue_bcg_body(d, prec, ctx->stream, false, 0));
+        else hbmc::enqueue_body(d, prec, ctx->stream, false, 0);
+      }
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(ctx->h_sc, d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
@@ -302,13 +334,15 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
     // SpMV, x/r update, 2 n_c sweeps, p update; after: gather, residual.
     // In graph mode the body runs `iters` times (at least once); in host
     // mode it is enqueued in groups of check_every.
-    const int64_t nc = d.nc, per = 3 + 2 * nc;
+    // BiCGStab: init = 2 gathers, residual, start; per iteration 7 kernels
+    // and two preconditioner applications (4 n_c sweeps).
+    const int64_t nc = d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc;
     int64_t passes = r.iters > 0 ? r.iters : 1;
     if (ctx->opt.loop_mode == HBMC_LOOP_HOST) {
       const int64_t every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
       passes = (passes + every - 1) / every * every;
     }
-    ctx->last_launches = (4 + 2 * nc) + passes * per + 2;
+    ctx->last_launches = (bicg ? 4 : 4 + 2 * nc) + passes * per + 2;
   }
   if (iters) *iters = r.iters;
   if (relres) *relres = r.relres;
@@ -411,6 +445,8 @@ void hbmc_destroy(hbmc_ctx *ctx) {
     for (int k = 0; k < 2; ++k) {
       if (ctx->exec[k]) cudaGraphExecDestroy(ctx->exec[k]);
       if (ctx->graph[k]) cudaGraphDestroy(ctx->graph[k]);
+      if (ctx->bexec[k]) cudaGraphExecDestroy(ctx->bexec[k]);
+      if (ctx->bgraph[k]) cudaGraphDestroy(ctx->bgraph[k]);
       if (ctx->cap[k]) cudaStreamDestroy(ctx->cap[k]);
     }
     for (void *p : ctx->allocs) cudaFree(p);
@@ -481,9 +517,13 @@ hbmc_status hbmc_ic0(hbmc_ctx *ctx, double shift, int64_t *bad_row) {
   if (bad_row) *bad_row = -1;
   TRY(need_device(ctx));
   if (!(shift > -1.0) || !(shift < 1e300)) return set_err(ctx, HBMC_ERR_INVALID_ARG, "shift must be > -1 and finite");
+  if (ctx->h.nonsym)
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "the context was built for nonsymmetric values: use hbmc_ilu0");
   ctx->factored = false;
+  ctx->factor_kind = 0;
   if (ctx->h.n == 0) {
     ctx->factored = true;
+    ctx->factor_kind = 1;
     return HBMC_OK;
   }
   DeviceGuard guard(ctx->device);
@@ -504,6 +544,59 @@ hbmc_status hbmc_ic0(hbmc_ctx *ctx, double shift, int64_t *bad_row) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->factored = true;
+  ctx->factor_kind = 1;
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_ilu0(hbmc_ctx *ctx, double shift, int64_t *bad_row) {
+  if (bad_row) *bad_row = -1;
+  TRY(need_device(ctx));
+  if (!(shift > -1.0) || !(shift < 1e300)) return set_err(ctx, HBMC_ERR_INVALID_ARG, "shift must be > -1 and finite");
+  if (!ctx->h.nonsym)
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "hbmc_ilu0 needs a context built with opt.nonsymmetric = 1");
+  ctx->factored = false;
+  ctx->factor_kind = 0;
+  if (ctx->h.n == 0) {
+    ctx->factored = true;
+    ctx->factor_kind = 2;
+    return HBMC_OK;
+  }
+  DeviceGuard guard(ctx->device);
+  const DeviceLayout &d = ctx->d;
+  hbmc::enqueue_ilu0(d, shift, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_sc, d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const long long bad = ctx->h_sc->bad_row;
+  if (bad != LLONG_MAX) {
+    int64_t orig = (bad >= 0 && bad < ctx->h.n_pad) ? ctx->h.inv[bad] : -1;
+    if (bad_row) *bad_row = orig;
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "ILU(0) pivot zero or not finite at row %lld (reordered %lld)",
+                  (long long)orig, (long long)bad);
+    return set_err(ctx, HBMC_ERR_NOT_SPD_PIVOT, buf);
+  }
+  hbmc::enqueue_unit_dinv(d, ctx->stream);
+  hbmc::enqueue_scatter_factor(d, true, ctx->stream, d.uval);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->factored = true;
+  ctx->factor_kind = 2;
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_get_factor_u(const hbmc_ctx *ctx_c, double *upper) {
+  hbmc_ctx *ctx = const_cast<hbmc_ctx *>(ctx_c);
+  TRY(need_device(ctx));
+  if (!ctx->factored || ctx->factor_kind != 2) return set_err(ctx, HBMC_ERR_NOT_FACTORED, "no ILU(0) factor");
+  if (!upper) return set_err(ctx, HBMC_ERR_INVALID_ARG, "null output");
+  DeviceGuard guard(ctx->device);
+  const HostLayout &h = ctx->h;
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> uv(h.nnz_lower);
+  if (h.nnz_lower) CK(cudaMemcpy(uv.data(), ctx->d.uval, sizeof(double) * h.nnz_lower, cudaMemcpyDeviceToHost));
+  std::memset(upper, 0, sizeof(double) * h.ci.size());
+  for (int64_t e = 0; e < h.nnz_lower; ++e) upper[h.u_to_abar[e]] = uv[e];
   return HBMC_OK;
 }
 
@@ -520,7 +613,9 @@ hbmc_status hbmc_get_factor(const hbmc_ctx *ctx_c, double *lower, double *diag) 
     std::memset(lower, 0, sizeof(double) * h.ci.size());
     for (int64_t e = 0; e < h.nnz_lower; ++e) lower[h.l_to_abar[e]] = lv[e];
   }
-  if (diag && h.n_pad) CK(cudaMemcpy(diag, ctx->d.ldiag, sizeof(double) * h.n_pad, cudaMemcpyDeviceToHost));
+  if (diag && h.n_pad)
+    CK(cudaMemcpy(diag, ctx->factor_kind == 2 ? ctx->d.udiag : ctx->d.ldiag, sizeof(double) * h.n_pad,
+                  cudaMemcpyDeviceToHost));
   return HBMC_OK;
 }
 
@@ -544,6 +639,15 @@ hbmc_status hbmc_iccg(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
   TRY(need_device(ctx));
   DeviceGuard guard(ctx->device);
   return solve_dev(ctx, b_dev, x_dev, tol, maxit, iters, relres, true_relres);
+}
+
+hbmc_status hbmc_bicgstab(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double tol, int64_t maxit,
+                          int64_t *iters, double *relres, double *true_relres) {
+  TRY(need_device(ctx));
+  if (ctx->h.n && !ctx->h.nonsym)
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "hbmc_bicgstab needs a context built with opt.nonsymmetric = 1");
+  DeviceGuard guard(ctx->device);
+  return solve_dev(ctx, b_dev, x_dev, tol, maxit, iters, relres, true_relres, true);
 }
 
 hbmc_status hbmc_iccg_host(hbmc_ctx *ctx, const double *b_host, double *x_host, double tol,

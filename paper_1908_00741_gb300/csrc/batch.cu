@@ -749,6 +749,7 @@ hbmc_status hbmc_batch_build(int32_t nsys, const hbmc_system *systems, int32_t b
   hbmc_default_options(&o);
   if (opt) o = *opt;
   if (o.host_only) return berr(nullptr, HBMC_ERR_INVALID_ARG, "batch: host_only is not supported");
+  if (o.nonsymmetric) return berr(nullptr, HBMC_ERR_INVALID_ARG, "batch: only symmetric systems (IC(0), CG)");
   if (o.precision != HBMC_PREC_F64 && o.precision != HBMC_PREC_F32)
     return berr(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
   o.sweep_kernel = 0;

@@ -26,7 +26,7 @@ bool fail(std::string &err, const char *msg, int64_t a = -1, int64_t b = -1) {
 }
 
 // CSR checks: shape, sorted unique columns, positive diagonal, exact symmetry.
-bool validate(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, std::string &err) {
+bool validate(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, bool nonsym, std::string &err) {
   if (n < 0) return fail(err, "n < 0");
   if (n == 0) return true;
   if (!rp || !ci || !v) return fail(err, "null CSR pointer");
@@ -42,7 +42,9 @@ bool validate(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, 
       if (e > rp[i] && ci[e - 1] >= j) return fail(err, "columns not strictly ascending", i, j);
       if (j == i) {
         diag = true;
-        if (!(v[e] > 0.0) || !(v[e] < 1e308)) return fail(err, "diagonal not positive and finite", i);
+        if (nonsym ? (v[e] == 0.0 || !(v[e] < 1e308 && v[e] > -1e308))
+                   : (!(v[e] > 0.0) || !(v[e] < 1e308)))
+          return fail(err, nonsym ? "diagonal zero or not finite" : "diagonal not positive and finite", i);
       }
       if (!(v[e] == v[e]) || v[e] > 1e308 || v[e] < -1e308) return fail(err, "non-finite value", i, j);
     }
@@ -55,7 +57,7 @@ bool validate(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, 
       const int32_t *lo = ci + rp[j], *hi = ci + rp[j + 1];
       const int32_t *f = std::lower_bound(lo, hi, (int32_t)i);
       if (f == hi || *f != i) return fail(err, "pattern not symmetric", i, j);
-      if (v[rp[j] + (f - lo)] != v[e]) return fail(err, "values not symmetric", i, j);
+      if (!nonsym && v[rp[j] + (f - lo)] != v[e]) return fail(err, "values not symmetric", i, j);
     }
   return true;
 }
@@ -203,7 +205,8 @@ hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const do
     fail(err, "w must be 1, 2, 4, 8, 16 or 32", w);
     return HBMC_ERR_INVALID_ARG;
   }
-  if (!validate(n, rp, ci, v, err)) return HBMC_ERR_INVALID_ARG;
+  const bool nonsym = opt.nonsymmetric != 0;
+  if (!validate(n, rp, ci, v, nonsym, err)) return HBMC_ERR_INVALID_ARG;
   if (opt.blocking == HBMC_BLOCK_BOXES) {
     if (opt.grid[0] < 1 || opt.grid[1] < 1 || opt.grid[2] < 1 ||
         opt.grid[0] * opt.grid[1] * opt.grid[2] != n) {
@@ -221,6 +224,7 @@ hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const do
   }
 
   h = HostLayout();
+  h.nonsym = nonsym;
   h.n = n;
   h.bs = bs;
   h.w = w;
@@ -316,6 +320,40 @@ hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const do
       h.lci[o] = h.ci[e];
       h.laval[o] = h.av[e];
       h.l_to_abar[o] = e;
+    }
+  }
+  if (nonsym) {
+    // transposed values: lower entry (k, c) <- abar_ck (row c, column k > c)
+    h.uaval.resize(h.nnz_lower);
+    h.u_to_abar.resize(h.nnz_lower);
+    for (int64_t k = 0; k < np; ++k)
+      for (int64_t o = h.lrp[k]; o < h.lrp[k + 1]; ++o) {
+        const int64_t c = h.lci[o];
+        const int32_t *lo = h.ci.data() + h.rp[c], *hi = h.ci.data() + h.rp[c + 1];
+        const int64_t e = h.rp[c] + (std::lower_bound(lo, hi, (int32_t)k) - lo);
+        h.uaval[o] = h.av[e];
+        h.u_to_abar[o] = e;
+      }
+    // upper rows: row i lists columns j > i ascending with the lower entry (j, i)
+    h.urp.assign(np + 1, 0);
+    for (int64_t i = 0; i < np; ++i) {
+      int64_t c = 0;
+      for (int64_t e = h.rp[i]; e < h.rp[i + 1]; ++e)
+        if (h.ci[e] > i) ++c;
+      h.urp[i + 1] = h.urp[i] + c;
+    }
+    h.uci.resize(h.urp[np]);
+    h.upos.resize(h.urp[np]);
+    for (int64_t i = 0; i < np; ++i) {
+      int64_t f = h.urp[i];
+      for (int64_t e = h.rp[i]; e < h.rp[i + 1]; ++e) {
+        const int64_t j = h.ci[e];
+        if (j <= i) continue;
+        const int32_t *lo = h.lci.data() + h.lrp[j], *hi = h.lci.data() + h.lrp[j + 1];
+        h.uci[f] = (int32_t)j;
+        h.upos[f] = h.lrp[j] + (std::lower_bound(lo, hi, (int32_t)i) - lo);
+        ++f;
+      }
     }
   }
 

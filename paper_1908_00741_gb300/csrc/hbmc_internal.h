@@ -42,6 +42,16 @@ struct HostLayout {
   std::vector<int64_t> l_to_abar;  // lower entry -> position in Abar
   std::vector<double> adiag;       // n_pad
 
+  // Nonsymmetric values (pattern still symmetric; ILU(0)): for lower entry
+  // e = (i, j) the transposed value abar_ji and its position in Abar; the
+  // upper triangle by rows (row i: columns j > i ascending, with the lower
+  // entry (j, i) that carries u_ij).
+  bool nonsym = false;
+  std::vector<double> uaval;
+  std::vector<int64_t> u_to_abar;
+  std::vector<int64_t> urp, upos;
+  std::vector<int32_t> uci;
+
   // SpMV: SELL with slice height w, column-major inside a slice
   std::vector<int64_t> a_ptr;  // nslices+1, entry offsets
   std::vector<int32_t> a_col;
@@ -98,6 +108,8 @@ hbmc_status make_ctx_from_layout(HostLayout &&h, const hbmc_options &opt, hbmc_c
 struct Scalars {
   double rho, rho_new, beta, pq, alpha, rr, bb, bnorm, relres, tol, true_relres;
   long long iters, maxit;
+  double omega, rho_old, rv, tt, ts;  // BiCGStab scalars
+  int half;    // BiCGStab: the half step met the tolerance (x += alpha ph still owed)
   int status;  // 0 running, 1 converged, 2 maxit reached, 3 breakdown
   int done;    // nonzero: every further kernel of the solve returns at once
   int zero_x;  // b == 0: the solution is x = 0
@@ -109,7 +121,7 @@ struct Scalars {
 };
 
 enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_BREAKDOWN = 3 };
-enum { CNT_RES = 0, CNT_PQ = 1, CNT_RR = 2, CNT_RZ = 3, CNT_TRUE = 4 };
+enum { CNT_RES = 0, CNT_PQ = 1, CNT_RR = 2, CNT_RZ = 3, CNT_TRUE = 4, CNT_S = 5, CNT_W = 6, CNT_RHO = 7 };
 
 // Shared-memory stage layout of the TMA-fed substitution kernels (byte
 // offsets inside one stage) for one direction and one value type.
@@ -204,9 +216,17 @@ struct DeviceLayout {
   int32_t *fo_col = nullptr, *bo_col = nullptr;
   uint8_t *fi_m = nullptr, *bi_m = nullptr;
   double *fo_val = nullptr, *fi_val = nullptr, *bo_val = nullptr, *bi_val = nullptr;
-  double *dinv = nullptr;
+  double *dinv = nullptr;   // forward sweep's diagonal scaling (1 / l_ii; all ones for ILU(0))
+  double *dinvb = nullptr;  // backward sweep's (1 / l_ii, the same array, for IC(0); 1 / u_ii for ILU(0))
   float *fo_val32 = nullptr, *fi_val32 = nullptr, *bo_val32 = nullptr, *bi_val32 = nullptr;
-  float *dinv32 = nullptr;
+  float *dinv32 = nullptr, *dinvb32 = nullptr;
+  // ILU(0) (nonsymmetric contexts): transposed values, upper rows, the U factor
+  int32_t nonsym = 0;
+  double *uaval = nullptr, *uval = nullptr, *udiag = nullptr;
+  int64_t *urp = nullptr, *upos = nullptr;
+  int32_t *uci = nullptr;
+  // BiCGStab vectors (nonsymmetric contexts; n_pad + kGuard each)
+  double *rh = nullptr, *sv = nullptr, *ph = nullptr;
   int64_t *lrp = nullptr;
   int32_t *lci = nullptr;
   double *laval = nullptr, *adiag = nullptr, *lval = nullptr, *ldiag = nullptr;

@@ -460,20 +460,22 @@ __global__ void __launch_bounds__(kSweepThreads)
 }
 
 // Spread the factor into the substitution layouts (and their FP32 copies).
+// lval feeds the forward layout, bval the backward one (the same array for
+// IC(0), whose U is L^T; U's values for ILU(0)).
 __global__ void k_scatter_factor(int64_t nnz_lower, const double *__restrict__ lval,
-                                 const int64_t *__restrict__ lmap_f,
+                                 const double *__restrict__ bval, const int64_t *__restrict__ lmap_f,
                                  const int64_t *__restrict__ lmap_b, double *fo, double *fi,
                                  double *bo, double *bi, float *fo32, float *fi32, float *bo32,
                                  float *bi32) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nnz_lower) return;
-  const double v = lval[e];
+  const double v = lval[e], u = bval[e];
   const int64_t f = lmap_f[e], b = lmap_b[e];
   if (f >= 0) fo[f] = v; else fi[-f - 1] = v;
-  if (b >= 0) bo[b] = v; else bi[-b - 1] = v;
+  if (b >= 0) bo[b] = u; else bi[-b - 1] = u;
   if (fo32) {
     if (f >= 0) fo32[f] = (float)v; else fi32[-f - 1] = (float)v;
-    if (b >= 0) bo32[b] = (float)v; else bi32[-b - 1] = (float)v;
+    if (b >= 0) bo32[b] = (float)u; else bi32[-b - 1] = (float)u;
   }
 }
 
@@ -544,11 +546,11 @@ SweepArgs<T> sweep_args(const DeviceLayout &d, bool fwd, int c) {
   if constexpr (sizeof(T) == 8) {
     a.o_val = (const T *)(fwd ? d.fo_val : d.bo_val);
     a.i_val = (const T *)(fwd ? d.fi_val : d.bi_val);
-    a.dinv = (const T *)d.dinv;
+    a.dinv = (const T *)(fwd ? d.dinv : d.dinvb);
   } else {
     a.o_val = (const T *)(fwd ? d.fo_val32 : d.bo_val32);
     a.i_val = (const T *)(fwd ? d.fi_val32 : d.bi_val32);
-    a.dinv = (const T *)d.dinv32;
+    a.dinv = (const T *)(fwd ? d.dinv32 : d.dinvb32);
   }
   a.bs = d.bs;
   a.w = d.w;
@@ -713,6 +715,8 @@ void enqueue_final(const DeviceLayout &d, cudaStream_t s) {
       d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, d.b, d.x, d.t, d.part, d.sc, d.hist);
 }
 
+void enqueue_reset_bad_row(const DeviceLayout &d, cudaStream_t s) { k_set_bad_row<<<1, 1, 0, s>>>(d.sc); }
+
 void enqueue_ic0(const DeviceLayout &d, double shift, cudaStream_t s) {
   k_set_bad_row<<<1, 1, 0, s>>>(d.sc);
   for (int c = 0; c < d.nc; ++c) {
@@ -722,13 +726,17 @@ void enqueue_ic0(const DeviceLayout &d, double shift, cudaStream_t s) {
   }
 }
 
-void enqueue_scatter_factor(const DeviceLayout &d, bool f32, cudaStream_t s) {
+void enqueue_scatter_factor(const DeviceLayout &d, bool f32, cudaStream_t s, const double *bval) {
+  if (!bval) bval = d.lval;
   if (d.nnz_lower > 0)
     k_scatter_factor<<<blocks_for(d.nnz_lower, kRowThreads), kRowThreads, 0, s>>>(
-        d.nnz_lower, d.lval, d.lmap_f, d.lmap_b, d.fo_val, d.fi_val, d.bo_val, d.bi_val,
+        d.nnz_lower, d.lval, bval, d.lmap_f, d.lmap_b, d.fo_val, d.fi_val, d.bo_val, d.bi_val,
         f32 ? d.fo_val32 : nullptr, f32 ? d.fi_val32 : nullptr, f32 ? d.bo_val32 : nullptr,
         f32 ? d.bi_val32 : nullptr);
-  if (f32) enqueue_narrow(d.dinv, d.dinv32, d.n_pad, s);
+  if (f32) {
+    enqueue_narrow(d.dinv, d.dinv32, d.n_pad, s);
+    if (d.dinvb != d.dinv) enqueue_narrow(d.dinvb, d.dinvb32, d.n_pad, s);
+  }
 }
 
 }  // namespace hbmc

@@ -84,6 +84,15 @@ void enqueue_relres(const DeviceLayout &d, cudaStream_t s);
 void enqueue_update_xr(const DeviceLayout &d, cudaStream_t s);
 void enqueue_update_p(const DeviceLayout &d, cudaStream_t s);
 void enqueue_ic0(const DeviceLayout &d, double shift, cudaStream_t s);
-void enqueue_scatter_factor(const DeviceLayout &d, bool f32, cudaStream_t s);
+void enqueue_scatter_factor(const DeviceLayout &d, bool f32, cudaStream_t s, const double *bval = nullptr);
+void enqueue_reset_bad_row(const DeviceLayout &d, cudaStream_t s);
+
+// ILU(0) and BiCGStab for nonsymmetric values (bicgstab.cu)
+void enqueue_ilu0(const DeviceLayout &d, double shift, cudaStream_t s);
+void enqueue_unit_dinv(const DeviceLayout &d, cudaStream_t s);
+void enqueue_bcg_init(const DeviceLayout &d, cudaStream_t s);
+cudaError_t enqueue_bcg_body(const DeviceLayout &d, int prec, cudaStream_t s, bool use_cond,
+                             cudaGraphConditionalHandle h);
+int64_t bcg_partials_needed(const DeviceLayout &d);
 
 }  // namespace hbmc

@@ -243,11 +243,11 @@ WArgs<T> warp_args(const DeviceLayout &d, bool fwd, int c, const WarpPlan &w) {
   if constexpr (sizeof(T) == 8) {
     a.o_val = (const T *)(fwd ? d.fo_val : d.bo_val);
     a.i_val = (const T *)(fwd ? d.fi_val : d.bi_val);
-    a.dinv = (const T *)d.dinv;
+    a.dinv = (const T *)(fwd ? d.dinv : d.dinvb);
   } else {
     a.o_val = (const T *)(fwd ? d.fo_val32 : d.bo_val32);
     a.i_val = (const T *)(fwd ? d.fi_val32 : d.bi_val32);
-    a.dinv = (const T *)d.dinv32;
+    a.dinv = (const T *)(fwd ? d.dinv32 : d.dinvb32);
   }
   a.bs = d.bs;
   a.tile0 = d.tile_ptr[c];

@@ -339,11 +339,11 @@ WideArgs<T> wide_args(const DeviceLayout &d, bool fwd, int c, const WidePlan &p)
   if constexpr (sizeof(T) == 8) {
     a.o_val = (const T *)(fwd ? d.fo_val : d.bo_val);
     a.i_val = (const T *)(fwd ? d.fi_val : d.bi_val);
-    a.dinv = (const T *)d.dinv;
+    a.dinv = (const T *)(fwd ? d.dinv : d.dinvb);
   } else {
     a.o_val = (const T *)(fwd ? d.fo_val32 : d.bo_val32);
     a.i_val = (const T *)(fwd ? d.fi_val32 : d.bi_val32);
-    a.dinv = (const T *)d.dinv32;
+    a.dinv = (const T *)(fwd ? d.dinv32 : d.dinvb32);
   }
   a.bs = d.bs;
   a.w = d.w;

@@ -45,7 +45,7 @@ EXPORTED = [
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
-    "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar",
+    "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar", "hbmc_ilu0", "hbmc_get_factor_u", "hbmc_bicgstab",
     "hbmc_batch_build", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
     "hbmc_batch_set_stream", "hbmc_batch_set_precision", "hbmc_batch_ic0", "hbmc_batch_iccg",
     "hbmc_batch_autotune", "hbmc_batch_features",
@@ -60,7 +60,8 @@ class Options(ctypes.Structure):
                 ("box", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("sweep_tpb", ctypes.c_int32), ("sweep_kernel", ctypes.c_int32)]
+                ("sweep_tpb", ctypes.c_int32), ("sweep_kernel", ctypes.c_int32),
+                ("nonsymmetric", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -121,6 +122,9 @@ def load():
             "hbmc_spmv_dot_static": (I32, [P, P, P, P]),
             "hbmc_sor": (I32, [P, P, P, D, I32, I32, P]),
             "hbmc_sor_bar": (I32, [P, P, P, D, I32, I32]),
+            "hbmc_ilu0": (I32, [P, D, P]),
+            "hbmc_get_factor_u": (I32, [P, P]),
+            "hbmc_bicgstab": (I32, [P, P, P, D, I64, P, P, P]),
             "hbmc_batch_build": (I32, [I32, P, I32, P, P]),
             "hbmc_batch_destroy": (None, [P]),
             "hbmc_batch_last_error": (ctypes.c_char_p, [P]),
@@ -224,7 +228,7 @@ class Context:
 
 def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
                loop_mode=LOOP_GRAPH, host_only=False, device=-1, check_every=16,
-               sweep_tpb=0, sweep_kernel=0) -> Context:
+               sweep_tpb=0, sweep_kernel=0, nonsymmetric=False) -> Context:
     """hbmc_build on a CSR (workloads.CSR or any object with n, row_ptr, col, val)."""
     lib = load()
     opt = Options()
@@ -243,6 +247,7 @@ def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
     opt.check_every = check_every
     opt.sweep_tpb = sweep_tpb
     opt.sweep_kernel = sweep_kernel
+    opt.nonsymmetric = 1 if nonsymmetric else 0
     rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     v = np.ascontiguousarray(A.val, dtype=np.float64)
@@ -329,6 +334,33 @@ def hbmc_iccg_host(ctx: Context, b: np.ndarray, x: np.ndarray, tol=1e-8, maxit=1
     it, rr, tr = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
     s = ctx._lib.hbmc_iccg_host(ctx.handle, _np_ptr(b), _np_ptr(x), float(tol), int(maxit),
                                 ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tr))
+    ctx.check(s, (OK, NOT_CONVERGED, ERR_BREAKDOWN))
+    return SolveResult(s, int(it.value), float(rr.value), float(tr.value))
+
+
+def hbmc_ilu0(ctx: Context, shift: float = 0.0):
+    """ILU(0) of a context built with nonsymmetric=True; returns (status,
+    bad_row in the original numbering or -1)."""
+    bad = ctypes.c_int64(-1)
+    s = ctx._lib.hbmc_ilu0(ctx.handle, float(shift), ctypes.byref(bad))
+    ctx.check(s, (OK, ERR_NOT_SPD_PIVOT))
+    return s, int(bad.value)
+
+
+def hbmc_get_factor_u(ctx: Context) -> np.ndarray:
+    """U's strict upper triangle on Abar's positions (see hbmc_get_matrix)."""
+    nnz = len(hbmc_get_matrix(ctx)[1])
+    out = np.empty(nnz)
+    ctx.check(ctx._lib.hbmc_get_factor_u(ctx.handle, _np_ptr(out)))
+    return out
+
+
+def hbmc_bicgstab(ctx: Context, b, x, tol=1e-8, maxit=10000) -> SolveResult:
+    """ILU(0)-preconditioned BiCGStab; device tensors b, x (x: initial guess
+    in, solution out)."""
+    it, rr, tr = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
+    s = ctx._lib.hbmc_bicgstab(ctx.handle, _dev_ptr(b, ctx.n, "b"), _dev_ptr(x, ctx.n, "x"), float(tol), int(maxit),
+                               ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tr))
     ctx.check(s, (OK, NOT_CONVERGED, ERR_BREAKDOWN))
     return SolveResult(s, int(it.value), float(rr.value), float(tr.value))
 
