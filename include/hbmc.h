@@ -64,7 +64,11 @@ enum { HBMC_PREC_F64 = 0, HBMC_PREC_F32 = 1 };
 enum {
   HBMC_LOOP_GRAPH = 0, /* one CUDA graph launch per solve; a device-side while node
                           runs the iterations, convergence decided on the GPU */
-  HBMC_LOOP_HOST = 1   /* host launches iterations and polls a device flag */
+  HBMC_LOOP_HOST = 1,  /* host launches iterations and polls a device flag */
+  HBMC_LOOP_PERSISTENT = 2 /* the whole CG solve in one persistent cooperative kernel with
+                              grid-wide barriers between the phases: for small systems, whose
+                              iterations the launches dominate (w = 32, else as
+                              HBMC_LOOP_GRAPH; BiCGStab runs as HBMC_LOOP_GRAPH) */
 };
 
 typedef struct hbmc_options {
@@ -72,7 +76,7 @@ typedef struct hbmc_options {
   int64_t grid[3];   /* nx, ny, nz for HBMC_BLOCK_BOXES (n must equal nx*ny*nz) */
   int32_t box[3];    /* bx, by, bz for HBMC_BLOCK_BOXES (bx*by*bz must equal bs) */
   int32_t precision; /* HBMC_PREC_F64 (default) or HBMC_PREC_F32 */
-  int32_t loop_mode; /* HBMC_LOOP_GRAPH (default) or HBMC_LOOP_HOST */
+  int32_t loop_mode; /* HBMC_LOOP_GRAPH (default), HBMC_LOOP_HOST or HBMC_LOOP_PERSISTENT */
   int32_t host_only; /* nonzero: compute the ordering and layouts on the host only,
                         touch no GPU (inspection and CPU tests) */
   int32_t device;    /* CUDA device ordinal; -1 = the current device */

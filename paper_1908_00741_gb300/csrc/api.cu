@@ -194,6 +194,9 @@ hbmc_status upload(hbmc_ctx *ctx) {
   CK(hbmc::setup_wide_kernels());
   hbmc::plan_sor(h, d);
   CK(hbmc::setup_sor());
+  CK(hbmc::setup_persistent());
+  if (h.nc > 0) TRY(dupload(ctx, d.tile_ptr_dev, h.tile_ptr));
+  TRY(dalloc(ctx, d.pbar, 4));
   if (d.sweep_kernel == 2) {
     std::vector<int32_t> rf, rb;
     hbmc::plan_tma(h, d.tma_f, d.tma_b, rf, rb);
@@ -304,7 +307,14 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
   init.user_x = x_dev;
   *ctx->h_sc = init;
   CK(cudaMemcpyAsync(d.sc, ctx->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
-  if (ctx->opt.loop_mode == HBMC_LOOP_GRAPH) {
+  const bool persistent =
+      !bicg && ctx->opt.loop_mode == HBMC_LOOP_PERSISTENT && hbmc::persistent_usable(d, prec);
+  if (persistent) {
+    hbmc::enqueue_gather_in(d, nullptr, d.b, 0, ctx->stream);
+    hbmc::enqueue_gather_in(d, nullptr, d.x, 1, ctx->stream);
+    CK(hbmc::enqueue_persistent(d, prec, ctx->stream));
+    hbmc::enqueue_final(d, ctx->stream);
+  } else if (ctx->opt.loop_mode != HBMC_LOOP_HOST) {
     cudaGraphExec_t *ex = bicg ? ctx->bexec : ctx->exec;
     if (!ex[prec]) TRY(build_graph(ctx, prec, bicg));
     CK(cudaGraphLaunch(ex[prec], ctx->stream));
@@ -342,7 +352,7 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
       const int64_t every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
       passes = (passes + every - 1) / every * every;
     }
-    ctx->last_launches = (bicg ? 4 : 4 + 2 * nc) + passes * per + 2;
+    ctx->last_launches = persistent ? 5 : (bicg ? 4 : 4 + 2 * nc) + passes * per + 2;
   }
   if (iters) *iters = r.iters;
   if (relres) *relres = r.relres;
@@ -398,7 +408,7 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
   if (opt) o = *opt;
   if (o.precision != HBMC_PREC_F64 && o.precision != HBMC_PREC_F32)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
-  if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST)
+  if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST && o.loop_mode != HBMC_LOOP_PERSISTENT)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown loop mode");
   if (o.sweep_kernel < 0 || o.sweep_kernel > 6)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..6");

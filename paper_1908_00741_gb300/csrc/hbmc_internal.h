@@ -184,6 +184,8 @@ struct DeviceLayout {
   int64_t n = 0, n_pad = 0, nnz_lower = 0;
   int32_t bs = 1, w = 1, nc = 0;
   std::vector<int64_t> tile_ptr;  // host copy, for launch geometry
+  int64_t *tile_ptr_dev = nullptr;  // device copy (persistent kernel)
+  unsigned *pbar = nullptr;         // persistent kernel's grid barrier: arrivals, generation, error
 
   // sweep launch geometry: level-1 blocks per CUDA block, and the largest
   // same-block coefficient run of one CUDA block (staged in shared memory

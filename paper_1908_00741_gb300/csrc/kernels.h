@@ -53,6 +53,11 @@ bool spmv_tma_usable(const DeviceLayout &d);
 int64_t spmv_tma_partials_needed(const DeviceLayout &d);
 void enqueue_spmv_tma(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);
 
+// The whole CG solve as one persistent cooperative kernel (persistent.cu)
+cudaError_t setup_persistent();
+bool persistent_usable(const DeviceLayout &d, int prec);
+cudaError_t enqueue_persistent(const DeviceLayout &d, int prec, cudaStream_t s);
+
 // SOR / symmetric SOR sweeps on the HBMC ordering (sor.cu)
 void plan_sor(const HostLayout &h, DeviceLayout &d);
 cudaError_t setup_sor();

@@ -38,6 +38,7 @@ PREC_F64 = 0
 PREC_F32 = 1
 LOOP_GRAPH = 0
 LOOP_HOST = 1
+LOOP_PERSISTENT = 2
 
 EXPORTED = [
     "hbmc_default_options", "hbmc_build", "hbmc_destroy", "hbmc_last_error",

@@ -127,7 +127,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("name,mk,bs,w,box", CASES)
-@pytest.mark.parametrize("loop_mode", [H.LOOP_GRAPH, H.LOOP_HOST])
+@pytest.mark.parametrize("loop_mode", [H.LOOP_GRAPH, H.LOOP_HOST, H.LOOP_PERSISTENT])
 def test_iccg_matches_oracle(lib, orc, name, mk, bs, w, box, loop_mode):
     A = mk()
     b, _ = W.rhs_from_solution(A, 0)
@@ -446,3 +446,40 @@ def test_full_size_algebraic(lib, orc, which):
     res32 = H.hbmc_iccg(ctx, dev(P.b), x, tol=1e-8)
     assert res32.status == H.OK and res32.true_relres < 1.1e-8
     assert abs(res32.iters - ref.iters) <= max(2, ref.iters // 20)
+
+
+@pytest.mark.parametrize("precision", [H.PREC_F64, H.PREC_F32])
+def test_persistent_solve_edge_cases(lib, orc, precision):
+    """The persistent cooperative solve: zero right-hand side, maxit 0 and 3,
+    restart from the solution, the FP32 substitutions, the 32^3 system."""
+    A = W.poisson7(6)
+    ctx = H.hbmc_build(A, 8, 32, box=(2, 2, 2), loop_mode=H.LOOP_PERSISTENT, precision=precision)
+    assert H.hbmc_ic0(ctx)[0] == H.OK
+    x = dev(np.ones(A.n))
+    r = H.hbmc_iccg(ctx, dev(np.zeros(A.n)), x)
+    assert r.status == H.OK and r.iters == 0 and np.all(host(x) == 0)
+    b, _ = W.rhs_from_solution(A, 0)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = H.hbmc_iccg(ctx, dev(b), x, maxit=0)
+    assert r.status == H.NOT_CONVERGED and r.iters == 0
+    an = orc.analyse(A, 8, 32, box=(2, 2, 2))
+    lval, _, dinv, _ = orc.factor(an, 0.0)
+    r = H.hbmc_iccg(ctx, dev(b), x, maxit=3)
+    ref = orc.pcg(an, lval, dinv, b, maxit=3)
+    assert r.status == H.NOT_CONVERGED and r.iters == 3
+    if precision == H.PREC_F64:
+        assert _rel(host(x), ref.x) <= 1e-12
+    P = W.poisson_problem(32, bs=8)
+    c32 = H.hbmc_build(P.A, 8, 32, box=P.box, loop_mode=H.LOOP_PERSISTENT, precision=precision)
+    assert H.hbmc_ic0(c32)[0] == H.OK
+    an = orc.analyse(P.A, 8, 32, box=P.box)
+    lval, _, dinv, _ = orc.factor(an, 0.0)
+    ref = orc.pcg(an, lval, dinv, P.b, tol=1e-8)
+    x = torch.zeros(P.A.n, dtype=torch.float64, device="cuda")
+    r = H.hbmc_iccg(c32, dev(P.b), x, tol=1e-8)
+    assert r.status == H.OK and r.true_relres < 1.1e-8
+    if precision == H.PREC_F64:
+        assert r.iters == ref.iters and _rel(host(x), ref.x) <= 1e-12
+    x2 = x.clone()
+    r2 = H.hbmc_iccg(c32, dev(P.b), x2, tol=1e-7)
+    assert r2.status == H.OK and r2.iters == 0
