@@ -13,6 +13,7 @@ steps in the paper's order:
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import dataclasses
 import os
@@ -64,6 +65,9 @@ def _load():
                 "orc_spmv": (None, [I, P, P, P, P, P]),
                 "orc_dot": (D, [I, P, P, P, C]),
                 "orc_pcg": (C, [I, P, P, P, P, P, P, P, I, P, C, D, I, P, P, P]),
+                "orc_split_plan": (I, [I, P, C, C, C, P, P, P]),
+                "orc_spmv_split": (None, [I, P, P, P, C, P, C, P, P]),
+                "orc_pcg_split": (C, [I, P, P, P, P, P, P, P, I, P, C, D, I, P, P, P, C, P, C]),
                 "orc_sor": (C, [I, P, P, P, P, P, D, I, C]),
                 "orc_ilu0": (I, [I, P, P, P, P, D, P, P, P, P]),
                 "orc_bwd_u": (None, [I, P, P, P, P, P, P]),
@@ -185,6 +189,35 @@ def spmv(row_ptr, col, val, p):
     rp, ci = _i64(row_ptr), _i32(col)
     q = np.empty(len(rp) - 1)
     _load().orc_spmv(len(rp) - 1, _p(rp), _p(ci), _p(_f64(val)), _p(_f64(p)), _p(q))
+    return q
+
+
+SplitPlan = collections.namedtuple("SplitPlan", "w piece cost head processed nsplit npieces")
+
+
+def split_plan(row_ptr, w, piece=64, cost=2):
+    """Head width per slice of w rows for the row-splitting SELL SpMV
+    (Section 5.2.2's remedy), pieces of at most `piece` entries, `cost` per
+    piece in the plan's cost model; see orc_split_plan."""
+    rp = _i64(row_ptr)
+    n = len(rp) - 1
+    if n % w:
+        raise ValueError("the row count must be a multiple of w")
+    head = np.zeros(n // w, dtype=np.int32)
+    nsplit = ctypes.c_int64(0)
+    npieces = ctypes.c_int64(0)
+    processed = _load().orc_split_plan(n, _p(rp), int(w), int(piece), int(cost), _p(head),
+                                       ctypes.byref(nsplit), ctypes.byref(npieces))
+    return SplitPlan(int(w), int(piece), int(cost), head, int(processed), int(nsplit.value),
+                     int(npieces.value))
+
+
+def spmv_split(row_ptr, col, val, plan: SplitPlan, p):
+    """q = A p with every row cut by `plan`: parts summed from zero, then added in order."""
+    rp, ci = _i64(row_ptr), _i32(col)
+    q = np.empty(len(rp) - 1)
+    _load().orc_spmv_split(len(rp) - 1, _p(rp), _p(ci), _p(_f64(val)), plan.w, _p(_i32(plan.head)),
+                           plan.piece, _p(_f64(p)), _p(q))
     return q
 
 
@@ -318,8 +351,10 @@ def factor(an: Analysis, shift=0.0):
     return ic0(an.row_ptr, an.col, an.val, shift)
 
 
-def pcg(an: Analysis, lval, dinv, b, tol=1e-8, maxit=10000, x0=None, dot_mode=DOT_SEQUENTIAL):
-    """IC(0)-PCG on Abar; b and x0 in original ordering."""
+def pcg(an: Analysis, lval, dinv, b, tol=1e-8, maxit=10000, x0=None, dot_mode=DOT_SEQUENTIAL,
+        split: SplitPlan | None = None):
+    """IC(0)-PCG on Abar; b and x0 in original ordering.  With `split`, the
+    iteration's q = A p is the row-splitting product (spmv_split)."""
     bbar = np.zeros(an.n_pad)
     bbar[an.pi] = b
     xbar = np.zeros(an.n_pad)
@@ -329,9 +364,16 @@ def pcg(an: Analysis, lval, dinv, b, tol=1e-8, maxit=10000, x0=None, dot_mode=DO
     iters = ctypes.c_int64(0)
     relres = ctypes.c_double(0.0)
     order = _i64(an.pi)
-    st = _load().orc_pcg(an.n_pad, _p(an.row_ptr), _p(an.col), _p(an.val), _p(_f64(lval)),
-                         _p(_f64(dinv)), _p(bbar), _p(xbar), len(order), _p(order), int(dot_mode),
-                         float(tol), int(maxit), ctypes.byref(iters), ctypes.byref(relres), _p(hist))
+    args = (an.n_pad, _p(an.row_ptr), _p(an.col), _p(an.val), _p(_f64(lval)), _p(_f64(dinv)),
+            _p(bbar), _p(xbar), len(order), _p(order), int(dot_mode), float(tol), int(maxit),
+            ctypes.byref(iters), ctypes.byref(relres), _p(hist))
+    if split is None:
+        st = _load().orc_pcg(*args)
+    else:
+        if split.w != an.w:
+            raise ValueError("the split plan's slice height must be the analysis' w")
+        head = _i32(split.head)
+        st = _load().orc_pcg_split(*args, split.w, _p(head), split.piece)
     if st == 3:
         raise ValueError("matrix is not structurally symmetric")
     return Solve(xbar[an.pi].copy(), int(iters.value), float(relres.value), int(st),
@@ -339,11 +381,13 @@ def pcg(an: Analysis, lval, dinv, b, tol=1e-8, maxit=10000, x0=None, dot_mode=DO
 
 
 def iccg(A, b, bs, w, box=None, hbmc=True, shift=0.0, tol=1e-8, maxit=10000, x0=None,
-         dot_mode=DOT_SEQUENTIAL, an=None):
-    """Full pipeline: analyse, factor, solve.  Returns (Solve, Analysis)."""
+         dot_mode=DOT_SEQUENTIAL, an=None, split=None):
+    """Full pipeline: analyse, factor, solve.  Returns (Solve, Analysis).
+    `split` = (piece, cost) solves with the row-splitting SpMV of that plan."""
     if an is None:
         an = analyse(A, bs, w, box=box, hbmc=hbmc)
+    plan = None if split is None else split_plan(an.row_ptr, an.w, *split)
     lval, ldiag, dinv, bad = factor(an, shift)
     if bad >= 0:
         return Solve(np.zeros(A.n), 0, float("nan"), 2, np.zeros(0), bad, np.zeros(an.n_pad)), an
-    return pcg(an, lval, dinv, b, tol, maxit, x0, dot_mode), an
+    return pcg(an, lval, dinv, b, tol, maxit, x0, dot_mode, split=plan), an

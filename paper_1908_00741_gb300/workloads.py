@@ -258,6 +258,65 @@ def vector_laplacian(m: int, seed: int, dominance: float = 1.05) -> CSR:
     return A
 
 
+def irregular_structural(m: int, seed: int, mean_refine: float = 0.11, keep_near: float = 0.65,
+                         dominance: float | None = None) -> CSR:
+    """3 DOF per node on an m^3 grid of nodes with an irregular, widely spread
+    number of couplings per node (unknown 3*node+d), shaped like a structural
+    FEM matrix such as Audikw_1: about 80 nonzeros per row on average, row
+    lengths spread with a coefficient of variation near 0.27.
+
+    Node u draws a refinement level rho_u = min(1, -mean_refine * ln(1 - U_u))
+    (exponential, stream `seed`).  Node pairs at Chebyshev distance 1 are
+    coupled with probability keep_near, pairs at distance 2 with probability
+    (rho_u + rho_v) / 2 (one uniform per pair, stream seed + 1 + k for the k-th
+    of the 62 forward offsets).  Each coupled pair e carries a random SPD 3x3
+    block S_e (stream seed + 1000 + k): A = sum_e (e_u - e_v)(e_u - e_v)^T (x) S_e,
+    plus a random SPD block on every node of the domain boundary (stream
+    seed + 999), so A is SPD and has the conditioning of a vector Laplacian.
+    With `dominance`, every scalar diagonal entry is then replaced by dominance
+    times the sum of |a_kl| over the rest of its row instead.
+    """
+    nn = m * m * m
+    idx = np.arange(nn, dtype=np.int64)
+    x = idx % m
+    y = (idx // m) % m
+    z = idx // (m * m)
+    rho = np.minimum(1.0, -mean_refine * np.log1p(-uniform(seed, nn)))
+    node_block = np.zeros((nn, 3, 3))
+    brow, bcol, bval = [], [], []
+    offsets = [(dz, dy, dx) for dz in range(-2, 3) for dy in range(-2, 3) for dx in range(-2, 3)
+               if (dz, dy, dx) > (0, 0, 0)]
+    for k, (dz, dy, dx) in enumerate(offsets):
+        xx, yy, zz = x + dx, y + dy, z + dz
+        inside = (xx >= 0) & (xx < m) & (yy >= 0) & (yy < m) & (zz >= 0) & (zz < m)
+        j = np.where(inside, xx + m * (yy + m * zz), 0)
+        u = uniform(seed + 1 + k, nn)
+        if max(abs(dx), abs(dy), abs(dz)) == 1:
+            keep = inside & (u < keep_near)
+        else:
+            keep = inside & (u < 0.5 * (rho + rho[j]))
+        a, b = idx[keep], j[keep]
+        S = _random_spd3(seed + 1000 + k, len(a))
+        np.add.at(node_block, a, S)
+        np.add.at(node_block, b, S)
+        brow.append(a); bcol.append(b); bval.append(-S)
+        brow.append(b); bcol.append(a); bval.append(-S)  # S_e is symmetric
+    bnd = (x == 0) | (x == m - 1) | (y == 0) | (y == m - 1) | (z == 0) | (z == m - 1)
+    node_block[bnd] += _random_spd3(seed + 999, int(bnd.sum()))
+    brow.append(idx); bcol.append(idx); bval.append(node_block)
+    br = np.concatenate(brow); bc = np.concatenate(bcol); bv = np.concatenate(bval)
+    d = np.arange(3)
+    rows = (3 * br[:, None, None] + d[None, :, None]) + 0 * d[None, None, :]
+    cols = (3 * bc[:, None, None] + d[None, None, :]) + 0 * d[None, :, None]
+    A = _assemble(3 * nn, rows.reshape(-1), cols.reshape(-1), bv.reshape(-1))
+    if dominance is not None:
+        rows_of = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+        is_diag = rows_of == A.col
+        offsum = np.bincount(rows_of, weights=np.where(is_diag, 0.0, np.abs(A.val)), minlength=A.n)
+        A.val[is_diag] = dominance * offsum
+    return A
+
+
 @dataclasses.dataclass
 class Problem:
     """A linear system with its right-hand side and the blocking hint it asks for."""
