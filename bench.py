@@ -773,6 +773,148 @@ def run_ilu(args):
     print(json.dumps(line), flush=True)
 
 
+def run_structural(args):
+    """The row-split SpMV (Section 5.2.2's remedy for SELL slices whose rows
+    differ much in length) on the Audikw_1-shaped stand-in: 68^3 nodes x 3 DOF
+    (943,296 unknowns, about 78M nonzeros, row lengths spread so that SELL
+    with slices of 4 / 8 rows processes about 26% / 39% more entries than CRS,
+    the paper's 28% / 40% for Audikw_1), natural order, algebraic blocking
+    bs = 8, w = 32.  A step is one hbmc_iccg call with the split SpMV
+    (pieces of 64 entries, piece cost 2); the same solve without splitting,
+    the SpMV alone in both layouts, and the processed entries are reported
+    beside it."""
+    import torch
+    from paper_1908_00741_gb300 import hbmc as H
+    from paper_1908_00741_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    piece = 64
+    P = W.structural_problem(args.structural_m)
+    A = P.A
+    stream = torch.cuda.current_stream()
+    ctxs = {}
+    for name, split in (("split", piece), ("plain", 0)):
+        c = H.hbmc_build(A, DEFAULT_BS, 32, device=local, sell_split=split)
+        H.hbmc_set_stream(c, stream)
+        st, bad = H.hbmc_ic0(c, 0.0)
+        assert st == H.OK, bad
+        ctxs[name] = c
+    ctx = ctxs["split"]
+    b = torch.tensor(P.b, device="cuda")
+    x = torch.zeros_like(b)
+
+    def solve(c):
+        x.zero_()
+        return H.hbmc_iccg(c, b, x, tol=TOL)
+
+    for _ in range(args.warmup):
+        res = solve(ctx)
+    assert res.status == H.OK, res
+    torch.cuda.synchronize()
+    barrier(dist)
+    with ClockSampler(local) as clk:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        launches = 0
+        for _ in range(args.steps):
+            res = solve(ctx)
+            launches += ctx.info()["last_launches"]
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = max_over_ranks(dist, ev[0].elapsed_time(ev[1]) / args.steps, "cuda")
+    err = float(np.max(np.abs(x.cpu().numpy() - P.x_star)) / np.max(np.abs(P.x_star)))
+
+    # the same solve without row splitting, and both with FP32 substitutions
+    others = {}
+    for name, c, prec in (("plain_f64", ctxs["plain"], H.PREC_F64), ("split_f32", ctx, H.PREC_F32),
+                          ("plain_f32", ctxs["plain"], H.PREC_F32)):
+        H.hbmc_set_precision(c, prec)
+        for _ in range(2):
+            r = solve(c)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record(stream)
+        for _ in range(reps):
+            r = solve(c)
+        e.record(stream)
+        torch.cuda.synchronize()
+        others[name] = {"ms": round(a.elapsed_time(e) / reps, 3), "iters": r.iters, "true_relres": r.true_relres}
+        H.hbmc_set_precision(c, H.PREC_F64)
+
+    # e2e through the host-buffer entry point
+    bh = torch.tensor(P.b).pin_memory().numpy()
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
+    H.hbmc_iccg_host(ctx, bh, xh, tol=TOL)
+    e2e = []
+    for _ in range(3):
+        xh[:] = 0.0
+        t = time.perf_counter()
+        H.hbmc_iccg_host(ctx, bh, xh, tol=TOL)
+        e2e.append((time.perf_counter() - t) * 1e3)
+    e2e_ms = max_over_ranks(dist, statistics.median(e2e), "cuda")
+
+    # one CG iteration's phases in both layouts (CUDA events around back-to-back runs)
+    prof = {}
+    for name, c in ctxs.items():
+        solve(c)
+        prof[name] = H.hbmc_profile_kernels(c, 20)
+    inf, inf0 = ctx.info(), ctxs["plain"].info()
+    peak, peak_kind = measured_peaks()
+    sp_bytes = spmv_bytes(A.n, A.nnz)
+    sp_fma = A.nnz + A.n
+    gbs = {k: sp_bytes / (prof[k]["spmv"] * 1e-3) / 1e9 for k in prof}
+    tfl = {k: 2 * sp_fma / (prof[k]["spmv"] * 1e-3) / 1e12 for k in prof}
+    roofline = {"bound": "hbm", "kernel": "k_spmv_pieces + k_spmv_split (q = A p, fused p.q)",
+                "achieved": round(gbs["split"], 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs["split"] / peak, 4), "traffic": None, "algorithmic_bytes": sp_bytes,
+                "peak_source": peak_kind,
+                "fp64": {"fma_per_launch": sp_fma, "achieved_tflops": round(tfl["split"], 4),
+                         "peak_tflops": FP64_NOMINAL_TFLOPS, "frac": round(tfl["split"] / FP64_NOMINAL_TFLOPS, 4),
+                         "peak_source": "nominal"}}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        an = oracle.analyse(A, DEFAULT_BS, 32)
+        lval, _, dinv, _ = oracle.factor(an, 0.0)
+        plan = oracle.split_plan(an.row_ptr, 32, piece, 2)
+        k = min(args.cpu_sample_iters, res.iters)
+        t = time.perf_counter()
+        s = oracle.pcg(an, lval, dinv, P.b, tol=TOL, maxit=k, split=plan)
+        dt = time.perf_counter() - t
+        cpu = {"value": round(dt / max(s.iters, 1) * res.iters * 1e3, 3), "unit": "ms", "cores": 1,
+               "kind": "oracle", "sample": f"{s.iters} split-SpMV PCG iterations of the structural solve "
+                                           f"({dt:.2f} s), scaled to {res.iters} iterations"}
+    if rank != 0:
+        return
+    line = {
+        "metric": "ICCG time to 1e-8 FP64 residual with the row-split SpMV", "value": round(ms, 4), "unit": "ms",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"irregular 3-DOF structural stand-in for Audikw_1, {args.structural_m}^3 nodes "
+                               f"({A.n} unknowns, {A.nnz} nonzeros), natural order, algebraic bs={DEFAULT_BS}, "
+                               f"w=32, row splitting with pieces of {piece}, tol {TOL:g}",
+                   "n": A.n, "nnz": A.nnz, "bs": DEFAULT_BS, "w": 32, "colors": inf["nc"],
+                   "l2": f"inputs larger than L2 (device working set {inf['device_bytes'] / 1e9:.2f} GB)"},
+        "iters": res.iters, "true_relres": res.true_relres, "max_rel_err_vs_xstar": err,
+        "ms_per_iter": round(ms / max(res.iters, 1), 4),
+        "processed_entries": {"crs": A.nnz, "sell": inf0["sell_entries_a"], "split": inf["sell_entries_split"],
+                              "sell_over_crs": round(inf0["sell_entries_a"] / A.nnz, 4),
+                              "split_over_crs": round(inf["sell_entries_split"] / A.nnz, 4),
+                              "split_rows": inf["split_rows"], "pieces": inf["split_pieces"]},
+        "spmv_ms": {k: round(v["spmv"], 4) for k, v in prof.items()},
+        "phase_ms": {k: {q: round(t, 4) for q, t in v.items()} for k, v in prof.items()},
+        "spmv_gbs_algorithmic": {k: round(v, 1) for k, v in gbs.items()},
+        "variants": others,
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 2 * A.n * 8,
+                "d2h_bytes_per_step": A.n * 8},
+        "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary(), "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -820,14 +962,16 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--bs", type=int, default=DEFAULT_BS)
     ap.add_argument("--workload", default="poisson128",
-                    choices=["poisson128", "batch", "learned", "orderings", "sor", "ilu"],
+                    choices=["poisson128", "batch", "learned", "orderings", "sor", "ilu", "structural"],
                     help="poisson128: the headline solve; batch: 256 uneven systems solved together; "
                          "learned: learned IC shift against the plain rule; orderings: MC, BMC and HBMC; "
-                         "sor: symmetric SOR sweeps; ilu: ILU(0)-BiCGStab on a nonsymmetric system")
+                         "sor: symmetric SOR sweeps; ilu: ILU(0)-BiCGStab on a nonsymmetric system; "
+                         "structural: the row-split SpMV on an Audikw_1-shaped matrix")
     ap.add_argument("--sor-sweeps", type=int, default=10)
     ap.add_argument("--learned-train", type=int, default=200)
     ap.add_argument("--learned-heldout", type=int, default=40)
     ap.add_argument("--veclap-m", type=int, default=100)
+    ap.add_argument("--structural-m", type=int, default=68)
     ap.add_argument("--hetero-m", type=int, default=96)
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
@@ -848,7 +992,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         {"batch": run_batch, "learned": run_learned, "orderings": run_orderings,
-         "sor": run_sor, "ilu": run_ilu}.get(args.workload, run_gpu)(args)
+         "sor": run_sor, "ilu": run_ilu, "structural": run_structural}.get(args.workload, run_gpu)(args)
 
 
 if __name__ == "__main__":

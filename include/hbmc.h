@@ -67,7 +67,8 @@ enum {
   HBMC_LOOP_HOST = 1,  /* host launches iterations and polls a device flag */
   HBMC_LOOP_PERSISTENT = 2 /* the whole CG solve in one persistent cooperative kernel with
                               grid-wide barriers between the phases: for small systems, whose
-                              iterations the launches dominate (w = 32, else as
+                              iterations the launches dominate (w = 32 and no row
+                              splitting, else as
                               HBMC_LOOP_GRAPH; BiCGStab runs as HBMC_LOOP_GRAPH) */
 };
 
@@ -105,6 +106,21 @@ typedef struct hbmc_options {
                            per level-1 block. */
   int32_t nonsymmetric; /* 0: A must be symmetric (IC(0), CG); 1: only the pattern must be
                            symmetric and the diagonal nonzero (ILU(0), BiCGStab) */
+  int32_t sell_split;   /* row splitting of the CG's SpMV (Section 5.2.2: SELL pads every row
+                           of a slice to the slice's longest row; the remedy splits the long
+                           rows).  0 = off (default).  P > 0: every slice of w rows gets a head
+                           width t in [1, longest row] minimising
+                             w*t + sum over rows longer than t of
+                                   (length - t) + sell_split_cost * ceil((length - t) / P)
+                           (the largest t among equal costs); a row keeps its first t entries
+                           in the slice and the rest is cut into pieces of P entries (the last
+                           shorter), stored as rows of their own sorted by length.  Each part
+                           is summed from zero in ascending column order with fused
+                           multiply-adds and the parts' sums are added in order, so the
+                           product differs from the unsplit one in rounding only.  Used by
+                           the SpMV of hbmc_iccg and hbmc_spmv_bar; the residuals and every
+                           other kernel keep the unsplit layout.  Needs w = 32 or less. */
+  int32_t sell_split_cost; /* the per-piece cost of the plan above, in entries (0 = 2) */
 } hbmc_options;
 
 /* Fills *opt with the defaults. */
@@ -129,6 +145,10 @@ typedef struct hbmc_info_t {
   size_t device_bytes;      /* device memory held by the context */
   int64_t last_iters;       /* iterations of the last hbmc_iccg call */
   int64_t last_launches;    /* kernels launched by the last hbmc_iccg call */
+  int64_t split_rows;       /* rows cut by the SpMV row splitting (0 without it) */
+  int64_t split_pieces;     /* pieces those rows were cut into */
+  int64_t sell_entries_split; /* stored entries of the split SpMV layout: heads plus the
+                                 pieces' slices, each with its padding (0 without it) */
 } hbmc_info_t;
 
 /*
@@ -179,6 +199,14 @@ hbmc_status hbmc_get_ordering(const hbmc_ctx *ctx, int64_t *pi, int64_t *color_p
  * col int32[nnz + n_pad - n], val double[nnz + n_pad - n], sorted columns.
  */
 hbmc_status hbmc_get_matrix(const hbmc_ctx *ctx, int64_t *row_ptr, int32_t *col, double *val);
+
+/*
+ * hbmc_get_split - the head width t of every slice of w rows of the split
+ * SpMV layout (hbmc_options.sell_split; Section 5.2.2's row splitting):
+ * head int32[n_pad / w].  Works for host_only contexts.  INVALID_ARG when the
+ * context was built without row splitting.
+ */
+hbmc_status hbmc_get_split(const hbmc_ctx *ctx, int32_t *head);
 
 /* Bind the context to a CUDA stream (a cudaStream_t, e.g. from
  * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */

@@ -119,6 +119,21 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dupload(ctx, d.a_ptr, h.a_ptr));
   TRY(dupload(ctx, d.a_col, h.a_col));
   TRY(dupload(ctx, d.a_val, h.a_val));
+  if (h.split_piece > 0) {
+    d.split = 1;
+    d.n_virt = (int64_t)(h.sp_ptr.size() - 1) * h.w;
+    TRY(dupload(ctx, d.sh_ptr, h.sh_ptr));
+    TRY(dupload(ctx, d.sh_col, h.sh_col));
+    TRY(dupload(ctx, d.sh_val, h.sh_val));
+    TRY(dupload(ctx, d.sp_ptr, h.sp_ptr));
+    TRY(dupload(ctx, d.sp_col, h.sp_col));
+    TRY(dupload(ctx, d.sp_val, h.sp_val));
+    TRY(dupload(ctx, d.sl_mask, h.sl_mask));
+    TRY(dupload(ctx, d.sl_first, h.sl_first));
+    TRY(dupload(ctx, d.cmb_ptr, h.cmb_ptr));
+    TRY(dupload(ctx, d.cmb_slot, h.cmb_slot));
+    TRY(dalloc(ctx, d.tsum, (size_t)std::max<int64_t>(d.n_virt, 1)));
+  }
   TRY(dupload(ctx, d.fo_ptr, h.fo_ptr));
   TRY(dupload(ctx, d.fi_ptr, h.fi_ptr));
   TRY(dupload(ctx, d.bo_ptr, h.bo_ptr));
@@ -346,7 +361,8 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
     // mode it is enqueued in groups of check_every.
     // BiCGStab: init = 2 gathers, residual, start; per iteration 7 kernels
     // and two preconditioner applications (4 n_c sweeps).
-    const int64_t nc = d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc;
+    // Row-split SpMV: one more launch for the pieces.
+    const int64_t nc = d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc + (d.split && d.n_virt > 0 ? 1 : 0);
     int64_t passes = r.iters > 0 ? r.iters : 1;
     if (ctx->opt.loop_mode == HBMC_LOOP_HOST) {
       const int64_t every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
@@ -410,6 +426,10 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
   if (o.loop_mode != HBMC_LOOP_GRAPH && o.loop_mode != HBMC_LOOP_HOST && o.loop_mode != HBMC_LOOP_PERSISTENT)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "unknown loop mode");
+  if (o.sell_split < 0 || o.sell_split_cost < 0)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sell_split and sell_split_cost must be >= 0");
+  if (o.sell_split > 0 && w > 32)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "row splitting needs w <= 32");
   if (o.sweep_kernel < 0 || o.sweep_kernel > 6)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..6");
   if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
@@ -486,6 +506,17 @@ hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info) {
   info->device_bytes = ctx->d.bytes;
   info->last_iters = ctx->last_iters;
   info->last_launches = ctx->last_launches;
+  info->split_rows = h.split_rows;
+  info->split_pieces = h.split_pieces;
+  info->sell_entries_split = h.split_piece > 0 ? (int64_t)(h.sh_col.size() + h.sp_col.size()) : 0;
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_get_split(const hbmc_ctx *ctx, int32_t *head) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  const HostLayout &h = ctx->h;
+  if (h.split_piece <= 0) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "the context was built without row splitting");
+  if (head && !h.split_head.empty()) std::memcpy(head, h.split_head.data(), sizeof(int32_t) * h.split_head.size());
   return HBMC_OK;
 }
 

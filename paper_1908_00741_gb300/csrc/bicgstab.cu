@@ -320,12 +320,12 @@ cudaError_t enqueue_bcg_body(const DeviceLayout &d, int prec, cudaStream_t s, bo
   enqueue_bwd(d, prec, nullptr, 0, true, s);
   cudaError_t e = cudaMemcpyAsync(d.ph, d.z, bytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
-  enqueue_spmv(d, d.ph, d.q, false, s);
+  enqueue_spmv_plain(d, d.ph, d.q, false, s);
   k_bcg_alpha<<<g, kBThreads, 0, s>>>(d.n_pad, d.rh, d.q, d.part, d.sc);
   k_bcg_s<<<g, kBThreads, 0, s>>>(d.n_pad, d.r, d.q, d.sv, d.part, d.sc, d.hist);
   enqueue_fwd(d, prec, d.sv, true, s);
   enqueue_bwd(d, prec, nullptr, 0, true, s);
-  enqueue_spmv(d, d.z, d.t, false, s);
+  enqueue_spmv_plain(d, d.z, d.t, false, s);
   k_bcg_omega<<<g, kBThreads, 0, s>>>(d.n_pad, d.t, d.sv, d.part, d.sc);
   k_bcg_xr<<<g, kBThreads, 0, s>>>(d.n_pad, d.ph, d.z, d.t, d.sv, d.rh, d.x, d.r, d.part, d.sc, d.hist,
                                    use_cond ? 1 : 0, h);

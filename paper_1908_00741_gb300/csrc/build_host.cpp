@@ -3,6 +3,8 @@
 // padding (Section 4.2), Abar = P A P^T (Section 3, Eq. "AB"), and the packed
 // device layouts (SELL with slice size w, Section 4.3.2).
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <cstdio>
 #include <functional>
 #include <queue>
@@ -154,6 +156,122 @@ int32_t color_blocks(int64_t n, const int64_t *rp, const int32_t *ci, int64_t nb
 }
 
 }  // namespace
+
+// Row splitting of the SpMV layout (Section 5.2.2: in SELL a slice's rows
+// are padded to its longest row; the remedy is to split rows that are much
+// longer than the others).  Slice s of w rows gets the head width t in
+// [1, longest row] of least cost
+//   w*t + sum over rows longer than t of (length - t) + cost * ceil((length - t) / P),
+// the largest t among equal costs.  Each row keeps its first min(length, t)
+// entries in the slice; the rest is cut into pieces of P entries (the last
+// one shorter).  The pieces become rows of their own: sorted by length,
+// longest first (ties by row, then piece), packed w to a slice.
+hbmc_status plan_split(HostLayout &h, int32_t P, int32_t cost, std::string &err) {
+  const int32_t w = h.w;
+  if (w > 32) {
+    fail(err, "row splitting needs w <= 32", w);
+    return HBMC_ERR_INVALID_ARG;
+  }
+  const int64_t ns = h.n_pad / w;
+  const int64_t guard = h.n_pad;
+  h.split_piece = P;
+  h.split_cost = cost;
+  h.split_head.assign(ns, 0);
+  h.sh_ptr.assign(ns + 1, 0);
+  h.sl_mask.assign(ns, 0u);
+  h.sl_first.assign(ns, 0);
+  struct Piece {
+    int64_t len, row, start;
+  };
+  std::vector<Piece> pieces;
+  std::vector<int64_t> len(w);
+  int64_t nsplit = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t mx = 0;
+    for (int32_t j = 0; j < w; ++j) {
+      len[j] = h.rp[s * w + j + 1] - h.rp[s * w + j];
+      mx = std::max(mx, len[j]);
+    }
+    // cost(t) for every t; keep the last minimum
+    int64_t t_best = mx, c_best = -1;
+    for (int64_t t = 1; t <= mx; ++t) {
+      int64_t c = (int64_t)w * t;
+      for (int32_t j = 0; j < w; ++j) {
+        const int64_t rest = len[j] - t;
+        if (rest > 0) c += rest + (int64_t)cost * ((rest + P - 1) / P);
+      }
+      if (c_best < 0 || c <= c_best) {
+        c_best = c;
+        t_best = t;
+      }
+    }
+    h.split_head[s] = (int32_t)t_best;
+    h.sh_ptr[s + 1] = h.sh_ptr[s] + t_best * w;
+    h.sl_first[s] = (int32_t)nsplit;
+    for (int32_t j = 0; j < w; ++j) {
+      if (len[j] <= t_best) continue;
+      h.sl_mask[s] |= 1u << j;
+      ++nsplit;
+      const int64_t row = s * w + j;
+      for (int64_t a = t_best; a < len[j]; a += P) pieces.push_back({std::min<int64_t>(P, len[j] - a), row, a});
+    }
+  }
+  if (nsplit >= INT32_MAX || (int64_t)pieces.size() >= INT32_MAX) {
+    fail(err, "too many split rows or pieces", (int64_t)pieces.size());
+    return HBMC_ERR_INVALID_ARG;
+  }
+  h.split_rows = nsplit;
+  h.split_pieces = (int64_t)pieces.size();
+  // heads
+  h.sh_col.assign(h.sh_ptr[ns], (int32_t)guard);
+  h.sh_val.assign(h.sh_ptr[ns], 0.0);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int32_t j = 0; j < w; ++j) {
+      const int64_t row = s * w + j, b = h.rp[row];
+      const int64_t e = std::min<int64_t>(h.rp[row + 1], b + h.split_head[s]);
+      for (int64_t k = b; k < e; ++k) {
+        const int64_t slot = h.sh_ptr[s] + (k - b) * w + j;
+        h.sh_col[slot] = h.ci[k];
+        h.sh_val[slot] = h.av[k];
+      }
+    }
+  // pieces as rows, longest first; pieces were generated in (row, start) order
+  std::vector<int64_t> order(pieces.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int64_t)k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t b) { return pieces[a].len > pieces[b].len; });
+  const int64_t nv = (int64_t)(pieces.size() + w - 1) / w * w;
+  const int64_t nts = nv / w;
+  h.sp_ptr.assign(nts + 1, 0);
+  for (int64_t k = 0; k < nts; ++k) h.sp_ptr[k + 1] = h.sp_ptr[k] + pieces[order[k * w]].len * w;
+  h.sp_col.assign(h.sp_ptr[nts], (int32_t)guard);
+  h.sp_val.assign(h.sp_ptr[nts], 0.0);
+  std::vector<int32_t> slot_of(pieces.size());
+  for (int64_t v = 0; v < (int64_t)order.size(); ++v) {
+    const Piece &pc = pieces[order[v]];
+    slot_of[order[v]] = (int32_t)v;
+    const int64_t k = v / w, j = v % w, b = h.rp[pc.row] + pc.start;
+    for (int64_t e = 0; e < pc.len; ++e) {
+      const int64_t slot = h.sp_ptr[k] + e * w + j;
+      h.sp_col[slot] = h.ci[b + e];
+      h.sp_val[slot] = h.av[b + e];
+    }
+  }
+  // the split rows' pieces, in row order then piece order (= generation order)
+  h.cmb_ptr.assign(nsplit + 1, 0);
+  h.cmb_slot.assign(pieces.size(), 0);
+  int64_t r = -1, prev_row = -1;
+  for (size_t k = 0; k < pieces.size(); ++k) {
+    if (pieces[k].row != prev_row) {
+      ++r;
+      prev_row = pieces[k].row;
+      h.cmb_ptr[r] = (int32_t)k;
+    }
+    h.cmb_slot[k] = slot_of[k];
+  }
+  h.cmb_ptr[nsplit] = (int32_t)pieces.size();
+  return HBMC_OK;
+}
 
 // Per-unit records (see HostLayout) from the slice pointer arrays.
 hbmc_status make_records(HostLayout &h, std::string &err) {
@@ -383,6 +501,11 @@ hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const do
         h.a_val[slot] = h.av[e];
       }
     }
+
+  if (opt.sell_split > 0) {
+    const hbmc_status st = plan_split(h, opt.sell_split, opt.sell_split_cost > 0 ? opt.sell_split_cost : 2, err);
+    if (st != HBMC_OK) return st;
+  }
 
   // Forward (rows of L): other-color entries in ascending column order, then
   // same-block entries in ascending step.  Backward (rows of U = L^T):

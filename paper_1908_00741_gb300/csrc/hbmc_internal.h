@@ -57,6 +57,20 @@ struct HostLayout {
   std::vector<int32_t> a_col;
   std::vector<double> a_val;
 
+  // SpMV with long rows split (hbmc_options.sell_split): per slice a head
+  // width; heads as SELL (sh_*); the cut-off pieces as rows of their own,
+  // sorted by length, w to a slice (sp_*); the split rows in slice order with
+  // their pieces' positions (cmb_*); per slice a lane mask of split rows and
+  // the index of its first split row.
+  int32_t split_piece = 0, split_cost = 0;
+  std::vector<int32_t> split_head;
+  std::vector<int64_t> sh_ptr, sp_ptr;
+  std::vector<int32_t> sh_col, sp_col;
+  std::vector<double> sh_val, sp_val;
+  std::vector<uint32_t> sl_mask;
+  std::vector<int32_t> sl_first, cmb_ptr, cmb_slot;
+  int64_t split_rows = 0, split_pieces = 0;
+
   // Substitution layouts, one slice per (level-1 block, step).  "o" = entries
   // coupling to other colors (gathered from global memory), "i" = entries
   // coupling to earlier (forward) / later (backward) steps of the same BMC
@@ -214,6 +228,15 @@ struct DeviceLayout {
   int64_t *a_ptr = nullptr;
   int32_t *a_col = nullptr;
   double *a_val = nullptr;
+  // split SpMV layout (split = 1 when built with hbmc_options.sell_split)
+  int32_t split = 0;
+  int64_t n_virt = 0;  // piece rows, a multiple of w
+  int64_t *sh_ptr = nullptr, *sp_ptr = nullptr;
+  int32_t *sh_col = nullptr, *sp_col = nullptr;
+  double *sh_val = nullptr, *sp_val = nullptr;
+  uint32_t *sl_mask = nullptr;
+  int32_t *sl_first = nullptr, *cmb_ptr = nullptr, *cmb_slot = nullptr;
+  double *tsum = nullptr;  // the pieces' sums, n_virt
   int64_t *fo_ptr = nullptr, *fi_ptr = nullptr, *bo_ptr = nullptr, *bi_ptr = nullptr;
   int32_t *fo_col = nullptr, *bo_col = nullptr;
   uint8_t *fi_m = nullptr, *bi_m = nullptr;

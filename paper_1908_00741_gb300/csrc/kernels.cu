@@ -165,6 +165,64 @@ __global__ void __launch_bounds__(kRowThreads)
   sc->alpha = sc->rho / s;
 }
 
+// Row-split SpMV (Section 5.2.2's remedy for slices whose rows differ much
+// in length).  First the pieces: every cut-off piece is a row of its own in
+// a SELL layout of slices of w pieces, summed from zero in ascending column
+// order.
+__global__ void __launch_bounds__(kRowThreads)
+    k_spmv_pieces(const int64_t *__restrict__ sp_ptr, const int32_t *__restrict__ sp_col,
+                  const double *__restrict__ sp_val, int w, int lw, int64_t n_virt, const double *p,
+                  double *tsum, const Scalars *sc) {
+  if (sc && sc->done) return;  // sc is given inside the CG loop only
+  FOR_ROWS(v, n_virt) tsum[v] = sell_row(sp_ptr, sp_col, sp_val, w, lw, v, p);
+}
+
+struct SplitArgs {
+  const int64_t *sh_ptr;
+  const int32_t *sh_col;
+  const double *sh_val;
+  const uint32_t *sl_mask;
+  const int32_t *sl_first, *cmb_ptr, *cmb_slot;
+  const double *tsum;
+};
+
+// Then every row: its head (the slice's first t entries, from zero, ascending
+// columns) plus, for a split row, its pieces' sums added in piece order --
+// the oracle's q_i = ((S_0 + S_1) + S_2) + ... -- with p.q and alpha as in
+// k_spmv.
+template <bool kDot>
+__global__ void __launch_bounds__(kRowThreads)
+    k_spmv_split(const SplitArgs a, int w, int lw, int64_t n_pad, const double *p, double *q, double *part,
+                 Scalars *sc) {
+  if (kDot && sc->done) return;
+  double pq = 0.0;
+  FOR_ROWS(row, n_pad) {
+    double acc = sell_row(a.sh_ptr, a.sh_col, a.sh_val, w, lw, row, p);
+    const int64_t s = row >> lw;
+    const int j = (int)(row & (w - 1));
+    const uint32_t mk = a.sl_mask[s];
+    if ((mk >> j) & 1u) {
+      const int k = a.sl_first[s] + __popc(mk & ((1u << j) - 1u));
+      for (int c = a.cmb_ptr[k]; c < a.cmb_ptr[k + 1]; ++c) acc = __dadd_rn(acc, a.tsum[a.cmb_slot[c]]);
+    }
+    q[row] = acc;
+    if (kDot) pq = fma(p[row], acc, pq);
+  }
+  if (!kDot) return;
+  double v = block_sum<kRowThreads>(pq);
+  if (!publish(part + blockIdx.x, &v, 1, &sc->cnt[CNT_PQ], gridDim.x)) return;
+  const double sum = gather_partials<kRowThreads>(part, gridDim.x, 1, 0);
+  if (threadIdx.x != 0) return;
+  sc->cnt[CNT_PQ] = 0;
+  sc->pq = sum;
+  if (!(sum > 0.0) || !finite(sum)) {
+    sc->status = ST_BREAKDOWN;
+    sc->done = 1;
+    return;
+  }
+  sc->alpha = sc->rho / sum;
+}
+
 // x += alpha p, r -= alpha q, ||r||^2, iteration count and stopping test.
 __global__ void __launch_bounds__(kRowThreads)
     k_update_xr(int64_t n_pad, const double *p, const double *q, double *x, double *r,
@@ -596,6 +654,23 @@ void enqueue_narrow(const double *src, float *dst, int64_t n, cudaStream_t s) {
 }
 
 void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s) {
+  if (d.split) {
+    if (d.n_virt > 0) {
+      const unsigned g = (unsigned)std::min<int64_t>(row_grid(d), blocks_for(d.n_virt, kRowThreads));
+      k_spmv_pieces<<<g, kRowThreads, 0, s>>>(d.sp_ptr, d.sp_col, d.sp_val, d.w, d.lw, d.n_virt, p, d.tsum,
+                                               dot ? d.sc : nullptr);
+    }
+    const SplitArgs a{d.sh_ptr, d.sh_col, d.sh_val, d.sl_mask, d.sl_first, d.cmb_ptr, d.cmb_slot, d.tsum};
+    if (dot)
+      k_spmv_split<true><<<row_grid(d), kRowThreads, 0, s>>>(a, d.w, d.lw, d.n_pad, p, q, d.part, d.sc);
+    else
+      k_spmv_split<false><<<row_grid(d), kRowThreads, 0, s>>>(a, d.w, d.lw, d.n_pad, p, q, d.part, d.sc);
+    return;
+  }
+  enqueue_spmv_plain(d, p, q, dot, s);
+}
+
+void enqueue_spmv_plain(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s) {
   if (spmv_tma_usable(d)) return enqueue_spmv_tma(d, p, q, dot, s);
   if (warp_spmv_usable(d)) return enqueue_spmv_warp(d, p, q, dot, s);
   if (dot)

@@ -79,7 +79,11 @@ void enqueue_gather_in(const DeviceLayout &d, const double *src, double *dst, in
 void enqueue_gather_out(const DeviceLayout &d, const double *src, double *dst, bool to_user, cudaStream_t s);
 void enqueue_widen(const float *src, double *dst, int64_t n, cudaStream_t s);
 void enqueue_narrow(const double *src, float *dst, int64_t n, cudaStream_t s);
+// q = A p (with p.q and alpha when dot): the row-split layout when the
+// context has one, else enqueue_spmv_plain.
 void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);
+// q = A p on the unsplit SELL layout.
+void enqueue_spmv_plain(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);
 void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
 void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s);
 void enqueue_init(const DeviceLayout &d, int prec, cudaStream_t s);

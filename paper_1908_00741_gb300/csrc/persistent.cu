@@ -424,7 +424,7 @@ cudaError_t setup_persistent() {
 }
 
 bool persistent_usable(const DeviceLayout &d, int prec) {
-  return d.w == 32 && d.rec_f && d.tile_ptr_dev && d.pbar && p_smem(d, prec) <= kPSmemBudget &&
+  return d.w == 32 && !d.split && d.rec_f && d.tile_ptr_dev && d.pbar && p_smem(d, prec) <= kPSmemBudget &&
          d.part_len >= 2 * (int64_t)d.sm_count;
 }
 

@@ -42,7 +42,7 @@ LOOP_PERSISTENT = 2
 
 EXPORTED = [
     "hbmc_default_options", "hbmc_build", "hbmc_destroy", "hbmc_last_error",
-    "hbmc_status_string", "hbmc_info", "hbmc_get_ordering", "hbmc_get_matrix",
+    "hbmc_status_string", "hbmc_info", "hbmc_get_ordering", "hbmc_get_matrix", "hbmc_get_split",
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
@@ -62,7 +62,8 @@ class Options(ctypes.Structure):
                 ("loop_mode", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("sweep_tpb", ctypes.c_int32), ("sweep_kernel", ctypes.c_int32),
-                ("nonsymmetric", ctypes.c_int32)]
+                ("nonsymmetric", ctypes.c_int32), ("sell_split", ctypes.c_int32),
+                ("sell_split_cost", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -72,7 +73,9 @@ class Info(ctypes.Structure):
                 ("sell_entries_a", ctypes.c_int64), ("sell_entries_l", ctypes.c_int64),
                 ("sell_entries_u", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("factored", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
-                ("last_iters", ctypes.c_int64), ("last_launches", ctypes.c_int64)]
+                ("last_iters", ctypes.c_int64), ("last_launches", ctypes.c_int64),
+                ("split_rows", ctypes.c_int64), ("split_pieces", ctypes.c_int64),
+                ("sell_entries_split", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -108,6 +111,7 @@ def load():
             "hbmc_info": (I32, [P, P]),
             "hbmc_get_ordering": (I32, [P, P, P, P, P]),
             "hbmc_get_matrix": (I32, [P, P, P, P]),
+            "hbmc_get_split": (I32, [P, P]),
             "hbmc_set_stream": (I32, [P, P]),
             "hbmc_set_precision": (I32, [P, I32]),
             "hbmc_ic0": (I32, [P, D, P]),
@@ -229,8 +233,10 @@ class Context:
 
 def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
                loop_mode=LOOP_GRAPH, host_only=False, device=-1, check_every=16,
-               sweep_tpb=0, sweep_kernel=0, nonsymmetric=False) -> Context:
-    """hbmc_build on a CSR (workloads.CSR or any object with n, row_ptr, col, val)."""
+               sweep_tpb=0, sweep_kernel=0, nonsymmetric=False, sell_split=0,
+               sell_split_cost=0) -> Context:
+    """hbmc_build on a CSR (workloads.CSR or any object with n, row_ptr, col, val).
+    sell_split = P > 0 splits the SpMV's long rows into a head and pieces of P."""
     lib = load()
     opt = Options()
     lib.hbmc_default_options(ctypes.byref(opt))
@@ -249,6 +255,8 @@ def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
     opt.sweep_tpb = sweep_tpb
     opt.sweep_kernel = sweep_kernel
     opt.nonsymmetric = 1 if nonsymmetric else 0
+    opt.sell_split = int(sell_split)
+    opt.sell_split_cost = int(sell_split_cost)
     rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     v = np.ascontiguousarray(A.val, dtype=np.float64)
@@ -284,6 +292,14 @@ def hbmc_get_matrix(ctx: Context):
     v = np.empty(max(nnz, 1), dtype=np.float64)
     ctx.check(ctx._lib.hbmc_get_matrix(ctx.handle, _np_ptr(rp), _np_ptr(ci), _np_ptr(v)))
     return rp, ci[:nnz], v[:nnz]
+
+
+def hbmc_get_split(ctx: Context):
+    """Head width of every slice of w rows of the row-split SpMV layout."""
+    inf = ctx.info()
+    head = np.empty(max(inf["n_pad"] // max(inf["w"], 1), 1), dtype=np.int32)
+    ctx.check(ctx._lib.hbmc_get_split(ctx.handle, _np_ptr(head)))
+    return head[: inf["n_pad"] // max(inf["w"], 1)]
 
 
 def hbmc_set_stream(ctx: Context, stream) -> None:

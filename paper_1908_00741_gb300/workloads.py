@@ -370,6 +370,15 @@ def vector_laplacian_problem(m: int, bs: int = 8, w: int = 32, seed: int = 3,
     return Problem(f"veclap_{m}^3_bs{bs}", A, b, xs, bs, w, None)
 
 
+def structural_problem(m: int = 68, bs: int = 8, w: int = 32, seed: int = 7, rhs_seed: int = 0) -> Problem:
+    """The irregular 3-DOF structural matrix on m^3 nodes (Audikw_1-shaped at
+    m = 68: 943,296 unknowns, about 78M nonzeros), natural order, algebraic
+    blocking, b = A x* with x* ~ U(-1, 1)."""
+    A = irregular_structural(m, seed)
+    b, xs = rhs_from_solution(A, rhs_seed)
+    return Problem(f"structural_{m}^3x3_bs{bs}", A, b, xs, bs, w, None)
+
+
 def convection_diffusion_problem(m: int, bs: int = 8, w: int = 32, velocity=(0.5, 0.3, 0.2),
                                  seed: int = 0) -> Problem:
     """Nonsymmetric convection-diffusion on m^3, geometric bs-cubes, b = A x*."""

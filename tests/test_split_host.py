@@ -1,0 +1,50 @@
+"""The host build's row-split SpMV plan (hbmc_build host_only with
+sell_split; Section 5.2.2's remedy) against the oracle's plan: head widths,
+split rows, pieces and processed entries equal; argument checks."""
+import numpy as np
+import pytest
+
+from paper_1908_00741_gb300 import hbmc as H
+from paper_1908_00741_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_00741_gb300 import _build
+    _build.build()
+    return H.load()
+
+
+HOST_CASES = [
+    ("structural_8_bs8_w32_P64", lambda: W.irregular_structural(8, 7), 8, 32, None, 64, 0),
+    ("structural_7_bs4_w16_P16_c1", lambda: W.irregular_structural(7, 2), 4, 16, None, 16, 1),
+    ("hetero27_9_rand_w8_P4_c3", lambda: W.permute_input(W.heterogeneous_stencil(9, 27, 2.0, 1),
+                                                         W.random_order(2, 729)), 8, 8, None, 4, 3),
+    ("poisson7_9_box_w32_P2", lambda: W.poisson7(9), 8, 32, (2, 2, 2), 2, 1),
+    ("veclap_5_rand_w1_P8", lambda: W.permute_input(W.vector_laplacian(5, 3), W.random_order(4, 375)),
+     8, 1, None, 8, 2),
+]
+
+
+@pytest.mark.parametrize("name,mk,bs,w,box,P,cost", HOST_CASES)
+def test_host_split_plan_matches_oracle(lib, orc, name, mk, bs, w, box, P, cost):
+    A = mk()
+    ctx = H.hbmc_build(A, bs, w, box=box, host_only=True, sell_split=P, sell_split_cost=cost)
+    an = orc.analyse(A, bs, w, box=box)
+    plan = orc.split_plan(an.row_ptr, w, P, cost if cost > 0 else 2)
+    np.testing.assert_array_equal(H.hbmc_get_split(ctx), plan.head)
+    inf = ctx.info()
+    assert (inf["split_rows"], inf["split_pieces"], inf["sell_entries_split"]) == \
+        (plan.nsplit, plan.npieces, plan.processed)
+
+
+def test_host_split_argument_checks(lib):
+    A = W.poisson7(4)
+    with pytest.raises(H.HbmcError):
+        H.hbmc_build(A, 8, 32, host_only=True, sell_split=-1)
+    with pytest.raises(H.HbmcError):
+        H.hbmc_build(A, 8, 32, host_only=True, sell_split=4, sell_split_cost=-2)
+    ctx = H.hbmc_build(A, 8, 32, host_only=True)
+    assert ctx.info()["sell_entries_split"] == 0
+    with pytest.raises(H.HbmcError):
+        H.hbmc_get_split(ctx)
