@@ -166,6 +166,7 @@ struct TwPlan {
 struct WidePlan {
   uint32_t off_ts = 0, off_tin = 0, off_ds = 0, off_rr = 0, off_oc = 0, off_vv = 0, off_gv = 0, off_iv = 0,
            off_im = 0, smem_bytes = 0;
+  int32_t chunk = 0;  // other-color entries staged per round (the whole run when it fits)
   bool ok = false;
 };
 

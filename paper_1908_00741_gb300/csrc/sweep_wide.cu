@@ -13,7 +13,11 @@
 //      parks coefficient and gathered value in shared memory; the same-block
 //      run is staged next to them;
 //   3. one thread per row adds its terms in the layout's order (farthest
-//      column from the diagonal first) out of shared memory;
+//      column from the diagonal first) out of shared memory.
+//   When the other-color run is too long for shared memory (rows of 80 to
+//   240 entries: a structural matrix), 2 and 3 repeat over groups of
+//   consecutive steps, as many as the staging area holds; a row's terms all
+//   lie in its own step's slice, so every row is still summed in one go.
 //   4. lanes j < w run the bs-step chains (Eqs. "y2-2", "y2-3");
 //   5. the rows are stored (backward: with the fused r.z).
 // The arithmetic and its order are those of every other sweep kernel, so
@@ -21,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 
@@ -53,36 +58,41 @@ struct WideArgs {
   const uint8_t *i_m;
   const T *i_val;
   const T *dinv;
-  int rec_ints, bs, w, lw;
+  int rec_ints, bs, w, lw, chunk;
   int64_t tile0;
   uint32_t off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_gv, off_iv, off_im;
 };
 
-// Phases 3-5, common to both ways of staging: in-order sums of the
-// other-color terms out of shared memory, the bs-step chains, the stores.
-template <int NT, bool FWD, typename T, typename OUT>
-__device__ __forceinline__ void wide_finish(const WideArgs<T> &a, unsigned char *smem, int64_t row0, OUT *out,
-                                            bool dot, double &rz, float *out32) {
-  const int32_t *rs = reinterpret_cast<const int32_t *>(smem + kWideRecOff);
+// Phase 3 for the rows of steps [l0, l1), whose other-color entries from
+// run position e_beg on are staged in vv / gv.
+template <int NT, typename T>
+__device__ __forceinline__ void wide_osum(const WideArgs<T> &a, unsigned char *smem, int l0, int l1, int e_beg) {
+  const int32_t *o_rel = reinterpret_cast<const int32_t *>(smem + kWideRecOff) + 6;
   T *ts = reinterpret_cast<T *>(smem + a.off_ts);
-  const T *ds = reinterpret_cast<const T *>(smem + a.off_ds);
-  const double *rr = reinterpret_cast<const double *>(smem + a.off_rr);
-  const T *vv = reinterpret_cast<const T *>(smem + a.off_vv);
-  const T *gv = reinterpret_cast<const T *>(smem + a.off_gv);
-  const T *iv = reinterpret_cast<const T *>(smem + a.off_iv);
-  const uint8_t *im = smem + a.off_im;
-  const int tid = threadIdx.x;
-  const int R = a.bs << a.lw;
-  // 3.
-  const int32_t *o_rel = rs + 6, *i_rel = rs + 7 + a.bs;
-  for (int lr = tid; lr < R; lr += NT) {
+  const T *vv = reinterpret_cast<const T *>(smem + a.off_vv) - e_beg;
+  const T *gv = reinterpret_cast<const T *>(smem + a.off_gv) - e_beg;
+  for (int lr = (l0 << a.lw) + (int)threadIdx.x; lr < (l1 << a.lw); lr += NT) {
     const int l = lr >> a.lw, j = lr & (a.w - 1);
     T acc = ts[lr];
     const int pe = o_rel[l + 1];
     for (int p = o_rel[l] + j; p < pe; p += a.w) acc = fma(-vv[p], gv[p], acc);
     ts[lr] = acc;
   }
-  __syncthreads();
+}
+
+// Phases 4-5, common to both ways of staging: the bs-step chains, the stores.
+template <int NT, bool FWD, typename T, typename OUT>
+__device__ __forceinline__ void wide_chain_store(const WideArgs<T> &a, unsigned char *smem, int64_t row0, OUT *out,
+                                                 bool dot, double &rz, float *out32) {
+  const int32_t *rs = reinterpret_cast<const int32_t *>(smem + kWideRecOff);
+  T *ts = reinterpret_cast<T *>(smem + a.off_ts);
+  const T *ds = reinterpret_cast<const T *>(smem + a.off_ds);
+  const double *rr = reinterpret_cast<const double *>(smem + a.off_rr);
+  const T *iv = reinterpret_cast<const T *>(smem + a.off_iv);
+  const uint8_t *im = smem + a.off_im;
+  const int tid = threadIdx.x;
+  const int R = a.bs << a.lw;
+  const int32_t *i_rel = rs + 7 + a.bs;
   // 4.
   if (tid < a.w) {
     const int j = tid;
@@ -128,38 +138,48 @@ __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *s
     if (!FWD && dot) rr[lr] = r[row0 + lr];
   }
   __syncthreads();
-  const int olen = rs[0], ilen = rs[1];
+  const int ilen = rs[1];
   const int64_t obeg = rec64(rs, 2), ibeg = rec64(rs, 4);
-  // 2.
-  for (int e0 = tid; e0 < olen; e0 += NT * kWideU) {
-    int32_t c[kWideU];
-    T v[kWideU], g[kWideU];
-#pragma unroll
-    for (int k = 0; k < kWideU; ++k) {
-      const int e = e0 + k * NT;
-      if (e < olen) {
-        c[k] = a.o_col[obeg + e];
-        v[k] = a.o_val[obeg + e];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kWideU; ++k)
-      if (e0 + k * NT < olen) g[k] = (T)gsrc[c[k]];
-#pragma unroll
-    for (int k = 0; k < kWideU; ++k) {
-      const int e = e0 + k * NT;
-      if (e < olen) {
-        vv[e] = v[k];
-        gv[e] = g[k];
-      }
-    }
-  }
+  const int32_t *o_rel = rs + 6;
   for (int e = tid; e < ilen; e += NT) {
     iv[e] = a.i_val[ibeg + e];
     im[e] = a.i_m[ibeg + e];
   }
-  __syncthreads();
-  wide_finish<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
+  // 2.-3., over groups of steps [l0, l1) whose entries fit in a.chunk (one
+  // group when the whole run does; the plan makes every single step fit)
+  for (int l0 = 0; l0 < a.bs;) {
+    int l1 = l0 + 1;
+    while (l1 < a.bs && o_rel[l1 + 1] - o_rel[l0] <= a.chunk) ++l1;
+    const int e_beg = o_rel[l0], e_end = o_rel[l1];
+    for (int e0 = e_beg + tid; e0 < e_end; e0 += NT * kWideU) {
+      int32_t c[kWideU];
+      T v[kWideU], g[kWideU];
+#pragma unroll
+      for (int k = 0; k < kWideU; ++k) {
+        const int e = e0 + k * NT;
+        if (e < e_end) {
+          c[k] = a.o_col[obeg + e];
+          v[k] = a.o_val[obeg + e];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kWideU; ++k)
+        if (e0 + k * NT < e_end) g[k] = (T)gsrc[c[k]];
+#pragma unroll
+      for (int k = 0; k < kWideU; ++k) {
+        const int e = e0 + k * NT;
+        if (e < e_end) {
+          vv[e - e_beg] = v[k];
+          gv[e - e_beg] = g[k];
+        }
+      }
+    }
+    __syncthreads();
+    wide_osum<NT, T>(a, smem, l0, l1, e_beg);
+    __syncthreads();
+    l0 = l1;
+  }
+  wide_chain_store<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
 }
 
 // The same with w = 32 and every contiguous operand moved by bulk copy
@@ -234,7 +254,9 @@ __device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned cha
       if (e0 + k * NT < olen) gv[e0 + k * NT] = g[k];
   }
   __syncthreads();
-  wide_finish<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
+  wide_osum<NT, T>(a, smem, 0, a.bs, 0);
+  __syncthreads();
+  wide_chain_store<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
   return true;
 }
 
@@ -298,7 +320,7 @@ uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
 // Shared-memory plan: plain-load staging (tma = false) or bulk-copy staging
 // (tma = true, w = 32; adds the column run and, for FP32 forward sweeps, a
 // double landing area for r).
-WidePlan plan_one(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o, int64_t max_i, size_t tsize) {
+WidePlan plan_whole(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o, int64_t max_i, size_t tsize) {
   WidePlan p;
   const uint64_t R = (uint64_t)bs * w;
   p.off_ts = a16((uint64_t)kWideRecOff + (uint64_t)kWideRecInts * 4);
@@ -318,6 +340,23 @@ WidePlan plan_one(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o
   const uint64_t total = a16(p.off_im + (uint64_t)max_i);
   p.smem_bytes = (uint32_t)std::min<uint64_t>(total, 0xffffffffu);
   p.ok = rec_ints <= (int)kWideRecInts && total <= kWideSmemBudget && (!tma || w == 32);
+  p.chunk = (int32_t)std::min<int64_t>(max_o, INT32_MAX);
+  return p;
+}
+
+// The whole other-color run staged at once when it fits; else (plain loads
+// only) as many entries per round as the budget leaves, if that holds the
+// longest single step's slice (max_step).
+WidePlan plan_one(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o, int64_t max_i, int64_t max_step,
+                  size_t tsize) {
+  WidePlan p = plan_whole(bs, w, fwd, tma, rec_ints, max_o, max_i, tsize);
+  if (p.ok || tma || rec_ints > (int)kWideRecInts) return p;
+  const WidePlan z = plan_whole(bs, w, fwd, false, rec_ints, 0, max_i, tsize);
+  if (z.smem_bytes + 64 >= kWideSmemBudget) return p;
+  const int64_t cap = (int64_t)(kWideSmemBudget - z.smem_bytes - 64) / (int64_t)(2 * tsize) / 32 * 32;
+  if (cap < max_step || cap < 32) return p;
+  p = plan_whole(bs, w, fwd, false, rec_ints, cap, max_i, tsize);
+  p.chunk = (int32_t)cap;
   return p;
 }
 
@@ -349,6 +388,7 @@ WideArgs<T> wide_args(const DeviceLayout &d, bool fwd, int c, const WidePlan &p)
   a.w = d.w;
   a.lw = d.lw;
   a.tile0 = d.tile_ptr[c];
+  a.chunk = p.chunk;
   a.off_ts = p.off_ts;
   a.off_tin = p.off_tin;
   a.off_ds = p.off_ds;
@@ -381,11 +421,20 @@ void plan_wide_kernels(const HostLayout &h, DeviceLayout &d) {
       pick[c] = (long_runs || u1 - u0 < 2 * (int64_t)d.sm_count) ? 1 : 0;
     }
   }
+  // the longest other-color slice of a single step, per direction
+  int64_t max_step[2] = {0, 0};
+  for (int dir = 0; dir < 2; ++dir) {
+    const std::vector<int32_t> &rec = dir == 0 ? h.rec_f : h.rec_b;
+    for (int64_t u = 0; u < h.ntiles; ++u) {
+      const int32_t *o_rel = rec.data() + (size_t)u * h.rec_ints + 6;
+      for (int l = 0; l < h.bs; ++l) max_step[dir] = std::max<int64_t>(max_step[dir], o_rel[l + 1] - o_rel[l]);
+    }
+  }
   for (int tma = 0; tma < 2; ++tma) {
-    (tma ? d.wt_f64_f : d.wd_f64_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, 8);
-    (tma ? d.wt_f64_b : d.wd_f64_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, 8);
-    (tma ? d.wt_f32_f : d.wd_f32_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, 4);
-    (tma ? d.wt_f32_b : d.wd_f32_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, 4);
+    (tma ? d.wt_f64_f : d.wd_f64_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, max_step[0], 8);
+    (tma ? d.wt_f64_b : d.wd_f64_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, max_step[1], 8);
+    (tma ? d.wt_f32_f : d.wd_f32_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, max_step[0], 4);
+    (tma ? d.wt_f32_b : d.wd_f32_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, max_step[1], 4);
   }
 }
 

@@ -28,6 +28,9 @@ CASES = [
     ("hetero7_6_bs1_w1", lambda: W.heterogeneous_stencil(6, 7, 1.5, 3), 1, 1, None),
     ("poisson7_6_bs64_w2", lambda: W.poisson7(6), 64, 2, None),
     ("poisson7_5_bs3_w2", lambda: W.poisson7(5), 3, 2, None),
+    # rows of 40-190 entries: the loader-thread sweeps stage the other-color
+    # runs (about 25k entries a level-1 block) in groups of steps
+    ("structural_8_bs8_w32", lambda: W.irregular_structural(8, 7), 8, 32, None),
 ]
 
 
