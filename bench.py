@@ -795,8 +795,9 @@ def run_structural(args):
     A = P.A
     stream = torch.cuda.current_stream()
     ctxs = {}
+    loop = H.LOOP_HOST if args.loop == "host" else H.LOOP_GRAPH
     for name, split in (("split", piece), ("plain", 0)):
-        c = H.hbmc_build(A, DEFAULT_BS, 32, device=local, sell_split=split)
+        c = H.hbmc_build(A, DEFAULT_BS, 32, device=local, sell_split=split, loop_mode=loop)
         H.hbmc_set_stream(c, stream)
         st, bad = H.hbmc_ic0(c, 0.0)
         assert st == H.OK, bad
@@ -829,8 +830,9 @@ def run_structural(args):
 
     # the same solve without row splitting, and both with FP32 substitutions
     others = {}
-    for name, c, prec in (("plain_f64", ctxs["plain"], H.PREC_F64), ("split_f32", ctx, H.PREC_F32),
-                          ("plain_f32", ctxs["plain"], H.PREC_F32)):
+    for name, c, prec in () if args.no_variants else (
+            ("plain_f64", ctxs["plain"], H.PREC_F64), ("split_f32", ctx, H.PREC_F32),
+            ("plain_f32", ctxs["plain"], H.PREC_F32)):
         H.hbmc_set_precision(c, prec)
         for _ in range(2):
             r = solve(c)

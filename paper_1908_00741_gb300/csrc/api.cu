@@ -173,6 +173,18 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dalloc(ctx, d.ldiag, h.n_pad));
   TRY(dupload(ctx, d.lmap_f, h.lmap_f));
   TRY(dupload(ctx, d.lmap_b, h.lmap_b));
+  TRY(dupload(ctx, d.fx_ptr, h.fx_ptr));
+  TRY(dupload(ctx, d.bx_ptr, h.bx_ptr));
+  TRY(dupload(ctx, d.fx_rel, h.fx_rel));
+  TRY(dupload(ctx, d.bx_rel, h.bx_rel));
+  TRY(dupload(ctx, d.fx_col, h.fx_col));
+  TRY(dupload(ctx, d.bx_col, h.bx_col));
+  TRY(dupload(ctx, d.lmapx_f, h.lmapx_f));
+  TRY(dupload(ctx, d.lmapx_b, h.lmapx_b));
+  TRY(dalloc(ctx, d.fx_val, h.fx_col.size()));
+  TRY(dalloc(ctx, d.bx_val, h.bx_col.size()));
+  TRY(dalloc(ctx, d.fx_val32, h.fx_col.size()));
+  TRY(dalloc(ctx, d.bx_val32, h.bx_col.size()));
   const size_t nv = (size_t)(h.n_pad + hbmc::kGuard);
   TRY(dalloc(ctx, d.b, nv));
   TRY(dalloc(ctx, d.x, nv));

@@ -587,6 +587,53 @@ hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const do
       }
     }
   }
+
+  // The same other-color entries without padding (loader-thread sweeps).
+  const int64_t ntl = h.ntiles;
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<int64_t> &xptr = dir == 0 ? h.fx_ptr : h.bx_ptr;
+    std::vector<int32_t> &xrel = dir == 0 ? h.fx_rel : h.bx_rel;
+    std::vector<int32_t> &xcol = dir == 0 ? h.fx_col : h.bx_col;
+    std::vector<int64_t> &lmapx = dir == 0 ? h.lmapx_f : h.lmapx_b;
+    int64_t &max_x = dir == 0 ? h.max_x_f : h.max_x_b;
+    int64_t &max_row = dir == 0 ? h.max_xrow_f : h.max_xrow_b;
+    const int64_t xstride = (tile_rows + 1 + 3) / 4 * 4;  // 16-byte rows of offsets
+    xptr.assign(ntl + 1, 0);
+    xrel.assign((size_t)ntl * xstride, 0);
+    lmapx.assign(h.nnz_lower, -1);
+    xcol.clear();
+    for (int64_t u = 0; u < ntl; ++u) {
+      const int64_t tbeg = u * tile_rows, tend = tbeg + tile_rows;
+      int32_t *rel = xrel.data() + (size_t)u * xstride;
+      int64_t len = 0;
+      for (int64_t lr = 0; lr < tile_rows; ++lr) {
+        const int64_t k = tbeg + lr;
+        rel[lr] = (int32_t)len;
+        const int64_t e0 = h.rp[k], e1 = h.rp[k + 1];
+        int64_t rl = 0;
+        for (int64_t q = 0; q < e1 - e0; ++q) {
+          const int64_t e = dir == 0 ? e0 + q : e1 - 1 - q;
+          const int64_t c = h.ci[e];
+          if (dir == 0 ? c >= k : c <= k) continue;
+          if (c >= tbeg && c < tend) continue;
+          lmapx[dir == 0 ? lower_index(k, c) : lower_index(c, k)] = xptr[u] + len;
+          xcol.push_back((int32_t)c);
+          ++len;
+          ++rl;
+        }
+        max_row = std::max(max_row, rl);
+      }
+      rel[tile_rows] = (int32_t)len;
+      if (len >= (int64_t(1) << 31) - 32) {
+        fail(err, "a level-1 block holds too many entries", u);
+        return HBMC_ERR_INVALID_ARG;
+      }
+      const int64_t padded = (len + 31) / 32 * 32;
+      xcol.resize(xptr[u] + padded, (int32_t)guard);
+      xptr[u + 1] = xptr[u] + padded;
+      max_x = std::max(max_x, padded);
+    }
+  }
   return make_records(h, err);
 }
 

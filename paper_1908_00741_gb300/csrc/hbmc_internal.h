@@ -82,6 +82,18 @@ struct HostLayout {
   // < 0: fi slot -v-1) and in the backward layout (bo / bi likewise)
   std::vector<int64_t> lmap_f, lmap_b;
 
+  // The other-color entries again, without slice padding, for the
+  // loader-thread sweeps: per level-1 block its rows one after another (row
+  // lr = step * w + lane; each row's entries in the order of fo / bo), the
+  // block's run padded to a multiple of 32 entries.  x_ptr: run starts
+  // (ntiles+1); x_rel: per level-1 block the R+1 row offsets inside its run
+  // (stored with a stride of R+1 rounded up to a multiple of 4);
+  // lmapx: lower entry -> slot, -1 for same-block entries.
+  std::vector<int64_t> fx_ptr, bx_ptr;
+  std::vector<int32_t> fx_rel, bx_rel, fx_col, bx_col;
+  std::vector<int64_t> lmapx_f, lmapx_b;
+  int64_t max_x_f = 0, max_x_b = 0, max_xrow_f = 0, max_xrow_b = 0;
+
   // Per level-1 block ("unit") records, rec_ints int32 each:
   //   [0] o_len, [1] i_len, [2..3] o_begin, [4..5] i_begin (int64 halves),
   //   [6 .. 6+bs] o_rel, [7+bs .. 7+2bs] i_rel
@@ -164,8 +176,8 @@ struct TwPlan {
 // Shared memory of the loader-thread sweeps (sweep_wide.cu), byte offsets;
 // ok = false when a level-1 block's runs do not fit.
 struct WidePlan {
-  uint32_t off_ts = 0, off_tin = 0, off_ds = 0, off_rr = 0, off_oc = 0, off_vv = 0, off_gv = 0, off_iv = 0,
-           off_im = 0, smem_bytes = 0;
+  uint32_t off_xr = 0, off_ts = 0, off_tin = 0, off_ds = 0, off_rr = 0, off_oc = 0, off_vv = 0, off_gv = 0,
+           off_iv = 0, off_im = 0, smem_bytes = 0;
   int32_t chunk = 0;  // other-color entries staged per round (the whole run when it fits)
   bool ok = false;
 };
@@ -257,6 +269,11 @@ struct DeviceLayout {
   int32_t *lci = nullptr;
   double *laval = nullptr, *adiag = nullptr, *lval = nullptr, *ldiag = nullptr;
   int64_t *lmap_f = nullptr, *lmap_b = nullptr;
+  // unpadded other-color runs of the loader-thread sweeps (HostLayout fx_*, bx_*)
+  int64_t *fx_ptr = nullptr, *bx_ptr = nullptr, *lmapx_f = nullptr, *lmapx_b = nullptr;
+  int32_t *fx_rel = nullptr, *bx_rel = nullptr, *fx_col = nullptr, *bx_col = nullptr;
+  double *fx_val = nullptr, *bx_val = nullptr;
+  float *fx_val32 = nullptr, *bx_val32 = nullptr;
   // vectors in HBMC order, n_pad + kGuard doubles (guard entries stay 0)
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
          *y = nullptr, *t = nullptr;

@@ -520,20 +520,28 @@ __global__ void __launch_bounds__(kSweepThreads)
 // Spread the factor into the substitution layouts (and their FP32 copies).
 // lval feeds the forward layout, bval the backward one (the same array for
 // IC(0), whose U is L^T; U's values for ILU(0)).
+struct ScatterArgs {
+  const int64_t *lmap_f, *lmap_b, *lmapx_f, *lmapx_b;
+  double *fo, *fi, *bo, *bi, *fx, *bx;
+  float *fo32, *fi32, *bo32, *bi32, *fx32, *bx32;  // null: no FP32 copies
+};
+
 __global__ void k_scatter_factor(int64_t nnz_lower, const double *__restrict__ lval,
-                                 const double *__restrict__ bval, const int64_t *__restrict__ lmap_f,
-                                 const int64_t *__restrict__ lmap_b, double *fo, double *fi,
-                                 double *bo, double *bi, float *fo32, float *fi32, float *bo32,
-                                 float *bi32) {
+                                 const double *__restrict__ bval, const ScatterArgs a) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nnz_lower) return;
   const double v = lval[e], u = bval[e];
-  const int64_t f = lmap_f[e], b = lmap_b[e];
-  if (f >= 0) fo[f] = v; else fi[-f - 1] = v;
-  if (b >= 0) bo[b] = u; else bi[-b - 1] = u;
-  if (fo32) {
-    if (f >= 0) fo32[f] = (float)v; else fi32[-f - 1] = (float)v;
-    if (b >= 0) bo32[b] = (float)u; else bi32[-b - 1] = (float)u;
+  const int64_t f = a.lmap_f[e], b = a.lmap_b[e];
+  const int64_t xf = a.lmapx_f ? a.lmapx_f[e] : -1, xb = a.lmapx_b ? a.lmapx_b[e] : -1;
+  if (f >= 0) a.fo[f] = v; else a.fi[-f - 1] = v;
+  if (b >= 0) a.bo[b] = u; else a.bi[-b - 1] = u;
+  if (xf >= 0) a.fx[xf] = v;
+  if (xb >= 0) a.bx[xb] = u;
+  if (a.fo32) {
+    if (f >= 0) a.fo32[f] = (float)v; else a.fi32[-f - 1] = (float)v;
+    if (b >= 0) a.bo32[b] = (float)u; else a.bi32[-b - 1] = (float)u;
+    if (xf >= 0) a.fx32[xf] = (float)v;
+    if (xb >= 0) a.bx32[xb] = (float)u;
   }
 }
 
@@ -803,11 +811,19 @@ void enqueue_ic0(const DeviceLayout &d, double shift, cudaStream_t s) {
 
 void enqueue_scatter_factor(const DeviceLayout &d, bool f32, cudaStream_t s, const double *bval) {
   if (!bval) bval = d.lval;
-  if (d.nnz_lower > 0)
-    k_scatter_factor<<<blocks_for(d.nnz_lower, kRowThreads), kRowThreads, 0, s>>>(
-        d.nnz_lower, d.lval, bval, d.lmap_f, d.lmap_b, d.fo_val, d.fi_val, d.bo_val, d.bi_val,
-        f32 ? d.fo_val32 : nullptr, f32 ? d.fi_val32 : nullptr, f32 ? d.bo_val32 : nullptr,
-        f32 ? d.bi_val32 : nullptr);
+  if (d.nnz_lower > 0) {
+    ScatterArgs a{d.lmap_f, d.lmap_b, d.lmapx_f, d.lmapx_b, d.fo_val, d.fi_val, d.bo_val, d.bi_val, d.fx_val,
+                  d.bx_val, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (f32) {
+      a.fo32 = d.fo_val32;
+      a.fi32 = d.fi_val32;
+      a.bo32 = d.bo_val32;
+      a.bi32 = d.bi_val32;
+      a.fx32 = d.fx_val32;
+      a.bx32 = d.bx_val32;
+    }
+    k_scatter_factor<<<blocks_for(d.nnz_lower, kRowThreads), kRowThreads, 0, s>>>(d.nnz_lower, d.lval, bval, a);
+  }
   if (f32) {
     enqueue_narrow(d.dinv, d.dinv32, d.n_pad, s);
     if (d.dinvb != d.dinv) enqueue_narrow(d.dinvb, d.dinvb32, d.n_pad, s);

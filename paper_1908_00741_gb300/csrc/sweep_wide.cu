@@ -14,10 +14,13 @@
 //      run is staged next to them;
 //   3. one thread per row adds its terms in the layout's order (farthest
 //      column from the diagonal first) out of shared memory.
-//   When the other-color run is too long for shared memory (rows of 80 to
-//   240 entries: a structural matrix), 2 and 3 repeat over groups of
-//   consecutive steps, as many as the staging area holds; a row's terms all
-//   lie in its own step's slice, so every row is still summed in one go.
+//   The other-color run is read from a copy without SELL padding: the
+//   level-1 block's rows one after another (a row's entries contiguous, in
+//   the same order), so rows of very unequal length -- the imbalance that
+//   Section 5.2.2 discusses for SELL -- cost their own entries only.  When
+//   the run is too long for shared memory (rows of 80 to 240 entries: a
+//   structural matrix), 2 and 3 repeat over groups of consecutive rows, as
+//   many as the staging area holds, each row summed in one go.
 //   4. lanes j < w run the bs-step chains (Eqs. "y2-2", "y2-3");
 //   5. the rows are stored (backward: with the fused r.z).
 // The arithmetic and its order are those of every other sweep kernel, so
@@ -52,32 +55,44 @@ constexpr int64_t kWideMinRun = 2048;
 
 template <typename T>
 struct WideArgs {
-  const int32_t *rec;
-  const int32_t *o_col;
-  const T *o_val;
+  const int32_t *rec;      // per level-1 block records (the same-block run)
+  const int64_t *x_ptr;    // unpadded other-color runs: starts
+  const int32_t *x_rel;    //   row offsets, x_stride ints per level-1 block
+  const int32_t *x_col;
+  const T *x_val;
   const uint8_t *i_m;
   const T *i_val;
   const T *dinv;
-  int rec_ints, bs, w, lw, chunk;
+  int rec_ints, bs, w, lw, chunk, x_stride;
   int64_t tile0;
-  uint32_t off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_gv, off_iv, off_im;
+  uint32_t off_xr, off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_gv, off_iv, off_im;
 };
 
-// Phase 3 for the rows of steps [l0, l1), whose other-color entries from
-// run position e_beg on are staged in vv / gv.
+// Phase 3 for rows [r0, r1), whose other-color entries from run position
+// e_beg on are staged in vv / gv.
 template <int NT, typename T>
-__device__ __forceinline__ void wide_osum(const WideArgs<T> &a, unsigned char *smem, int l0, int l1, int e_beg) {
-  const int32_t *o_rel = reinterpret_cast<const int32_t *>(smem + kWideRecOff) + 6;
+__device__ __forceinline__ void wide_osum(const WideArgs<T> &a, unsigned char *smem, int r0, int r1, int e_beg) {
+  const int32_t *xr = reinterpret_cast<const int32_t *>(smem + a.off_xr);
   T *ts = reinterpret_cast<T *>(smem + a.off_ts);
   const T *vv = reinterpret_cast<const T *>(smem + a.off_vv) - e_beg;
   const T *gv = reinterpret_cast<const T *>(smem + a.off_gv) - e_beg;
-  for (int lr = (l0 << a.lw) + (int)threadIdx.x; lr < (l1 << a.lw); lr += NT) {
-    const int l = lr >> a.lw, j = lr & (a.w - 1);
+  for (int lr = r0 + (int)threadIdx.x; lr < r1; lr += NT) {
     T acc = ts[lr];
-    const int pe = o_rel[l + 1];
-    for (int p = o_rel[l] + j; p < pe; p += a.w) acc = fma(-vv[p], gv[p], acc);
+    const int pe = xr[lr + 1];
+    for (int p = xr[lr]; p < pe; ++p) acc = fma(-vv[p], gv[p], acc);
     ts[lr] = acc;
   }
+}
+
+// The last row r1 > r0 such that rows [r0, r1) fit in `chunk` staged
+// entries (xr ascending; the plan makes every single row fit).
+__device__ __forceinline__ int rows_fitting(const int32_t *xr, int r0, int R, int chunk) {
+  int lo = r0 + 1, hi = R;  // xr[lo] - xr[r0] <= chunk holds
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (xr[mid] - xr[r0] <= chunk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 // Phases 4-5, common to both ways of staging: the bs-step chains, the stores.
@@ -119,6 +134,7 @@ __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *s
                                           const G *gsrc, OUT *out, const double *r, bool dot, double &rz,
                                           float *out32 = nullptr) {
   int32_t *rs = reinterpret_cast<int32_t *>(smem + kWideRecOff);
+  int32_t *xr = reinterpret_cast<int32_t *>(smem + a.off_xr);
   T *ts = reinterpret_cast<T *>(smem + a.off_ts);
   T *ds = reinterpret_cast<T *>(smem + a.off_ds);
   double *rr = reinterpret_cast<double *>(smem + a.off_rr);
@@ -132,6 +148,9 @@ __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *s
   // 1.
   const int32_t *rc = a.rec + u * a.rec_ints;
   for (int k = tid; k < a.rec_ints; k += NT) rs[k] = rc[k];
+  const int32_t *xg = a.x_rel + u * a.x_stride;
+  for (int k = tid; k <= R; k += NT) xr[k] = xg[k];
+  const int64_t xbeg = a.x_ptr[u];
   for (int lr = tid; lr < R; lr += NT) {
     ts[lr] = (T)in[row0 + lr];
     ds[lr] = a.dinv[row0 + lr];
@@ -139,18 +158,16 @@ __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *s
   }
   __syncthreads();
   const int ilen = rs[1];
-  const int64_t obeg = rec64(rs, 2), ibeg = rec64(rs, 4);
-  const int32_t *o_rel = rs + 6;
+  const int64_t ibeg = rec64(rs, 4);
   for (int e = tid; e < ilen; e += NT) {
     iv[e] = a.i_val[ibeg + e];
     im[e] = a.i_m[ibeg + e];
   }
-  // 2.-3., over groups of steps [l0, l1) whose entries fit in a.chunk (one
-  // group when the whole run does; the plan makes every single step fit)
-  for (int l0 = 0; l0 < a.bs;) {
-    int l1 = l0 + 1;
-    while (l1 < a.bs && o_rel[l1 + 1] - o_rel[l0] <= a.chunk) ++l1;
-    const int e_beg = o_rel[l0], e_end = o_rel[l1];
+  // 2.-3., over groups of rows [r0, r1) whose entries fit in a.chunk (one
+  // group when the whole run does)
+  for (int r0 = 0; r0 < R;) {
+    const int r1 = rows_fitting(xr, r0, R, a.chunk);
+    const int e_beg = xr[r0], e_end = xr[r1];
     for (int e0 = e_beg + tid; e0 < e_end; e0 += NT * kWideU) {
       int32_t c[kWideU];
       T v[kWideU], g[kWideU];
@@ -158,8 +175,8 @@ __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *s
       for (int k = 0; k < kWideU; ++k) {
         const int e = e0 + k * NT;
         if (e < e_end) {
-          c[k] = a.o_col[obeg + e];
-          v[k] = a.o_val[obeg + e];
+          c[k] = a.x_col[xbeg + e];
+          v[k] = a.x_val[xbeg + e];
         }
       }
 #pragma unroll
@@ -175,9 +192,9 @@ __device__ __forceinline__ void wide_unit(const WideArgs<T> &a, unsigned char *s
       }
     }
     __syncthreads();
-    wide_osum<NT, T>(a, smem, l0, l1, e_beg);
+    wide_osum<NT, T>(a, smem, r0, r1, e_beg);
     __syncthreads();
-    l0 = l1;
+    r0 = r1;
   }
   wide_chain_store<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
 }
@@ -194,6 +211,7 @@ __device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned cha
                                               Scalars *sc, float *out32 = nullptr) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   int32_t *rs = reinterpret_cast<int32_t *>(smem + kWideRecOff);
+  int32_t *xr = reinterpret_cast<int32_t *>(smem + a.off_xr);
   T *ts = reinterpret_cast<T *>(smem + a.off_ts);
   IN *tin = reinterpret_cast<IN *>(smem + a.off_tin);  // == ts when IN is T
   T *ds = reinterpret_cast<T *>(smem + a.off_ds);
@@ -207,24 +225,29 @@ __device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned cha
   const uint32_t R = (uint32_t)a.bs * 32u;
   const int64_t row0 = u * (int64_t)R;
   const bool want_r = !FWD && dot;
+  const uint32_t xbytes = (uint32_t)a.x_stride * 4u;
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_fence_init();
-    mbar_expect_tx(bar, R * (uint32_t)(sizeof(IN) + sizeof(T)) + (want_r ? R * 8u : 0u));
+    mbar_expect_tx(bar, R * (uint32_t)(sizeof(IN) + sizeof(T)) + (want_r ? R * 8u : 0u) + xbytes);
     tma_load_1d(tin, in + row0, R * (uint32_t)sizeof(IN), bar);
     tma_load_1d(ds, a.dinv + row0, R * (uint32_t)sizeof(T), bar);
     if (want_r) tma_load_1d(rr, r + row0, R * 8u, bar);
+    tma_load_1d(xr, a.x_rel + u * a.x_stride, xbytes, bar);
   }
   const int32_t *rc = a.rec + u * a.rec_ints;
   for (int k = tid; k < a.rec_ints; k += NT) rs[k] = rc[k];
+  __shared__ int64_t s_x[2];
+  if (tid < 2) s_x[tid] = a.x_ptr[u + tid];
   __syncthreads();
-  const int olen = rs[0], ilen = rs[1];
-  const int64_t obeg = rec64(rs, 2), ibeg = rec64(rs, 4);
+  const int ilen = rs[1];
+  const int64_t ibeg = rec64(rs, 4), xbeg = s_x[0];
+  const uint32_t xlen = (uint32_t)(s_x[1] - s_x[0]);  // a multiple of 32 entries
   if (tid == 0) {
-    mbar_arrive_expect_tx(bar, (uint32_t)olen * (uint32_t)(4 + sizeof(T)) + (uint32_t)ilen * (uint32_t)(1 + sizeof(T)));
-    if (olen > 0) {
-      tma_load_1d(oc, a.o_col + obeg, (uint32_t)olen * 4u, bar);
-      tma_load_1d(vv, a.o_val + obeg, (uint32_t)olen * (uint32_t)sizeof(T), bar);
+    mbar_arrive_expect_tx(bar, xlen * (uint32_t)(4 + sizeof(T)) + (uint32_t)ilen * (uint32_t)(1 + sizeof(T)));
+    if (xlen > 0) {
+      tma_load_1d(oc, a.x_col + xbeg, xlen * 4u, bar);
+      tma_load_1d(vv, a.x_val + xbeg, xlen * (uint32_t)sizeof(T), bar);
     }
     if (ilen > 0) {
       tma_load_1d(iv, a.i_val + ibeg, (uint32_t)ilen * (uint32_t)sizeof(T), bar);
@@ -244,6 +267,7 @@ __device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned cha
   if constexpr (!std::is_same<IN, T>::value) {
     for (int lr = tid; lr < (int)R; lr += NT) ts[lr] = (T)tin[lr];
   }
+  const int olen = xr[R];
   for (int e0 = tid; e0 < olen; e0 += NT * kWideU) {
     T g[kWideU];
 #pragma unroll
@@ -254,7 +278,7 @@ __device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned cha
       if (e0 + k * NT < olen) gv[e0 + k * NT] = g[k];
   }
   __syncthreads();
-  wide_osum<NT, T>(a, smem, 0, a.bs, 0);
+  wide_osum<NT, T>(a, smem, 0, R, 0);
   __syncthreads();
   wide_chain_store<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
   return true;
@@ -317,13 +341,18 @@ __global__ void __launch_bounds__(NT)
 
 uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
 
+// Row offsets of a level-1 block's unpadded run: R + 1 ints, padded to a
+// multiple of 4 (16 bytes) so that each block's offsets can be bulk-copied.
+int x_stride_of(int bs, int w) { return (bs * w + 1 + 3) / 4 * 4; }
+
 // Shared-memory plan: plain-load staging (tma = false) or bulk-copy staging
 // (tma = true, w = 32; adds the column run and, for FP32 forward sweeps, a
 // double landing area for r).
 WidePlan plan_whole(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o, int64_t max_i, size_t tsize) {
   WidePlan p;
   const uint64_t R = (uint64_t)bs * w;
-  p.off_ts = a16((uint64_t)kWideRecOff + (uint64_t)kWideRecInts * 4);
+  p.off_xr = a16((uint64_t)kWideRecOff + (uint64_t)kWideRecInts * 4);
+  p.off_ts = a16(p.off_xr + (uint64_t)x_stride_of(bs, w) * 4);
   uint64_t next = p.off_ts + R * tsize;
   p.off_tin = p.off_ts;
   if (tma && fwd && tsize != 8) {
@@ -346,7 +375,7 @@ WidePlan plan_whole(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max
 
 // The whole other-color run staged at once when it fits; else (plain loads
 // only) as many entries per round as the budget leaves, if that holds the
-// longest single step's slice (max_step).
+// longest row (max_step).
 WidePlan plan_one(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o, int64_t max_i, int64_t max_step,
                   size_t tsize) {
   WidePlan p = plan_whole(bs, w, fwd, tma, rec_ints, max_o, max_i, tsize);
@@ -373,14 +402,17 @@ WideArgs<T> wide_args(const DeviceLayout &d, bool fwd, int c, const WidePlan &p)
   WideArgs<T> a;
   a.rec = fwd ? d.rec_f : d.rec_b;
   a.rec_ints = d.rec_ints;
-  a.o_col = fwd ? d.fo_col : d.bo_col;
+  a.x_ptr = fwd ? d.fx_ptr : d.bx_ptr;
+  a.x_rel = fwd ? d.fx_rel : d.bx_rel;
+  a.x_col = fwd ? d.fx_col : d.bx_col;
+  a.x_stride = x_stride_of(d.bs, d.w);
   a.i_m = fwd ? d.fi_m : d.bi_m;
   if constexpr (sizeof(T) == 8) {
-    a.o_val = (const T *)(fwd ? d.fo_val : d.bo_val);
+    a.x_val = (const T *)(fwd ? d.fx_val : d.bx_val);
     a.i_val = (const T *)(fwd ? d.fi_val : d.bi_val);
     a.dinv = (const T *)(fwd ? d.dinv : d.dinvb);
   } else {
-    a.o_val = (const T *)(fwd ? d.fo_val32 : d.bo_val32);
+    a.x_val = (const T *)(fwd ? d.fx_val32 : d.bx_val32);
     a.i_val = (const T *)(fwd ? d.fi_val32 : d.bi_val32);
     a.dinv = (const T *)(fwd ? d.dinv32 : d.dinvb32);
   }
@@ -389,6 +421,7 @@ WideArgs<T> wide_args(const DeviceLayout &d, bool fwd, int c, const WidePlan &p)
   a.lw = d.lw;
   a.tile0 = d.tile_ptr[c];
   a.chunk = p.chunk;
+  a.off_xr = p.off_xr;
   a.off_ts = p.off_ts;
   a.off_tin = p.off_tin;
   a.off_ds = p.off_ds;
@@ -421,20 +454,12 @@ void plan_wide_kernels(const HostLayout &h, DeviceLayout &d) {
       pick[c] = (long_runs || u1 - u0 < 2 * (int64_t)d.sm_count) ? 1 : 0;
     }
   }
-  // the longest other-color slice of a single step, per direction
-  int64_t max_step[2] = {0, 0};
-  for (int dir = 0; dir < 2; ++dir) {
-    const std::vector<int32_t> &rec = dir == 0 ? h.rec_f : h.rec_b;
-    for (int64_t u = 0; u < h.ntiles; ++u) {
-      const int32_t *o_rel = rec.data() + (size_t)u * h.rec_ints + 6;
-      for (int l = 0; l < h.bs; ++l) max_step[dir] = std::max<int64_t>(max_step[dir], o_rel[l + 1] - o_rel[l]);
-    }
-  }
+  // unpadded runs: the longest level-1 block run and the longest row
   for (int tma = 0; tma < 2; ++tma) {
-    (tma ? d.wt_f64_f : d.wd_f64_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, max_step[0], 8);
-    (tma ? d.wt_f64_b : d.wd_f64_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, max_step[1], 8);
-    (tma ? d.wt_f32_f : d.wd_f32_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_o_f, h.max_i_f, max_step[0], 4);
-    (tma ? d.wt_f32_b : d.wd_f32_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_o_b, h.max_i_b, max_step[1], 4);
+    (tma ? d.wt_f64_f : d.wd_f64_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_x_f, h.max_i_f, h.max_xrow_f, 8);
+    (tma ? d.wt_f64_b : d.wd_f64_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_x_b, h.max_i_b, h.max_xrow_b, 8);
+    (tma ? d.wt_f32_f : d.wd_f32_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_x_f, h.max_i_f, h.max_xrow_f, 4);
+    (tma ? d.wt_f32_b : d.wd_f32_b) = plan_one(h.bs, h.w, false, tma, h.rec_ints, h.max_x_b, h.max_i_b, h.max_xrow_b, 4);
   }
 }
 
