@@ -100,7 +100,12 @@ typedef struct hbmc_options {
                                wave of CUDA blocks);
                            5 = the bulk-copy-staged warp kernels of 0 for every color;
                            6 = as 4 with the runs read by plain loads instead of bulk
-                               copies (the form 4 uses when w < 32). 
+                               copies (the form 4 uses when w < 32);
+                           7 = as 6 with each level-1 block's other-color sums spread over
+                               bs CUDA blocks, one per step, the last of which to finish
+                               runs the chains (automatic under 0 for colors with fewer
+                               than two level-1 blocks per SM whose other-color runs
+                               average 12288 or more entries).
                            SpMV (w = 32) is fed by bulk copies when a chunk of its slices fits
                            in shared memory, else one thread per row; with 3 it runs one warp
                            per level-1 block. */

@@ -181,6 +181,8 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dupload(ctx, d.bx_col, h.bx_col));
   TRY(dupload(ctx, d.lmapx_f, h.lmapx_f));
   TRY(dupload(ctx, d.lmapx_b, h.lmapx_b));
+  TRY(dalloc(ctx, d.ucnt, (size_t)std::max<int64_t>(h.ntiles, 1)));
+  CK(cudaMemset(d.ucnt, 0, sizeof(unsigned) * (size_t)std::max<int64_t>(h.ntiles, 1)));
   TRY(dalloc(ctx, d.fx_val, h.fx_col.size()));
   TRY(dalloc(ctx, d.bx_val, h.bx_col.size()));
   TRY(dalloc(ctx, d.fx_val32, h.fx_col.size()));
@@ -442,8 +444,8 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sell_split and sell_split_cost must be >= 0");
   if (o.sell_split > 0 && w > 32)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "row splitting needs w <= 32");
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 6)
-    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..6");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 7)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..7");
   if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_tpb must be 0 or a power of two with sweep_tpb * w <= 256");
   hbmc_ctx *ctx = nullptr;

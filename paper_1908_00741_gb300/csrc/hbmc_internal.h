@@ -232,7 +232,9 @@ struct DeviceLayout {
   SorPlan sor;
   WidePlan wd_f64_f, wd_f64_b, wd_f32_f, wd_f32_b;  // plain-load staging
   WidePlan wt_f64_f, wt_f64_b, wt_f32_f, wt_f32_b;  // bulk-copy staging (w = 32)
-  std::vector<uint8_t> wide_f, wide_b;  // per color: the loader-thread sweep is the faster one
+  WidePlan ws_f64_f, ws_f64_b, ws_f32_f, ws_f32_b;  // split over several CUDA blocks per level-1 block
+  std::vector<uint8_t> wide_f, wide_b;  // per color: 1 = loader-thread sweep, 2 = its split form
+  unsigned *ucnt = nullptr;  // per level-1 block arrival counters of the split form (zero between launches)
   int32_t lw = 0;        // log2(w)
   int64_t max_in_f = 0, max_in_b = 0;
   int32_t in_smem_f = 0, in_smem_b = 0;

@@ -52,6 +52,8 @@ constexpr uint64_t kWideWaitNs = 4000000000ull;
 // 128^3 (7-point, runs of 768 entries) the warp kernels win; on the 27-point
 // and 3-DOF matrices in a random order (runs of 5000-9000) these do.
 constexpr int64_t kWideMinRun = 2048;
+// ... and their split form when the unpadded runs average this many entries.
+constexpr int64_t kSplitMinRun = 12288;
 
 template <typename T>
 struct WideArgs {
@@ -64,6 +66,8 @@ struct WideArgs {
   const T *i_val;
   const T *dinv;
   int rec_ints, bs, w, lw, chunk, x_stride;
+  int gsteps;      // split variant: steps per CUDA block
+  unsigned *ucnt;  // split variant: per level-1 block arrival counters (zero between launches)
   int64_t tile0;
   uint32_t off_xr, off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_gv, off_iv, off_im;
 };
@@ -284,6 +288,39 @@ __device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned cha
   return true;
 }
 
+// r.z of a backward sweep: this CUDA block's partial into part[slot]; in
+// the last launch of the sweep, the last of its `nparts` contributing blocks
+// adds every partial of the sweep (part_total) in index order.
+__device__ __forceinline__ void bwd_dot_tail(double rz, Scalars *sc, int dot_mode, double *part, int64_t slot,
+                                             int last_launch, int64_t part_total, unsigned nparts) {
+  const double v = block_sum_rt(rz);
+  if (threadIdx.x == 0) part[slot] = v;
+  if (!last_launch) return;
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
+    s_last = (t == nparts - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
+  const double rho_new = block_sum_rt(acc);
+  if (threadIdx.x != 0) return;
+  sc->cnt[CNT_RZ] = 0;
+  sc->rho_new = rho_new;
+  if (sc->timeout) return;
+  if (!(rho_new > 0.0) || !finite(rho_new)) {
+    sc->status = ST_BREAKDOWN;
+    sc->done = 1;
+    return;
+  }
+  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
+  sc->rho = rho_new;
+}
+
 template <typename T, typename Y, int NT, bool TMA>
 __global__ void __launch_bounds__(NT)
     k_fwd_wide(const WideArgs<T> a, const double *__restrict__ r, Y *y, Scalars *sc, int check_done) {
@@ -311,32 +348,134 @@ __global__ void __launch_bounds__(NT)
     wide_unit<NT, false, T, Y, T, double>(a, smem, a.tile0 + blockIdx.x, yin, zgather<T>(z, z32), z, r,
                                           dot_mode != 0, rz, z32);
   if (!dot_mode) return;
-  const double v = block_sum_rt(rz);
-  if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
-  if (!last_launch) return;
-  __shared__ unsigned s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
-    s_last = (t == gridDim.x - 1);
+  bwd_dot_tail(rz, sc, dot_mode, part, part_off + blockIdx.x, last_launch, part_total, gridDim.x);
+}
+
+// Split variant (colors with few, long level-1 blocks): CUDA block b works
+// on level-1 block u = b / G_n, steps [g G, g G + G) with g = b % G_n.  It
+// stages and sums the other-color terms of those rows (phases 2-3, every row
+// in one go, the same operations as above) and parks the sums in the output
+// rows.  The last CUDA block of u to finish (an arrival counter; no block
+// waits for another) reads the R sums back and runs the chains and the
+// stores (phases 4-5).  So a level-1 block's gathers spread over G_n SMs
+// instead of one.  Returns true in the level-1 block's last CUDA block.
+template <int NT, bool FWD, typename T, typename IN, typename G, typename OUT>
+__device__ __forceinline__ bool wsplit_unit(const WideArgs<T> &a, unsigned char *smem, int64_t u, int g,
+                                            const IN *in, const G *gsrc, OUT *out, const double *r, bool dot,
+                                            double &rz, float *out32) {
+  int32_t *rs = reinterpret_cast<int32_t *>(smem + kWideRecOff);
+  int32_t *xr = reinterpret_cast<int32_t *>(smem + a.off_xr);
+  T *ts = reinterpret_cast<T *>(smem + a.off_ts);
+  T *ds = reinterpret_cast<T *>(smem + a.off_ds);
+  double *rr = reinterpret_cast<double *>(smem + a.off_rr);
+  T *vv = reinterpret_cast<T *>(smem + a.off_vv);
+  T *gv = reinterpret_cast<T *>(smem + a.off_gv);
+  T *iv = reinterpret_cast<T *>(smem + a.off_iv);
+  uint8_t *im = smem + a.off_im;
+  __shared__ unsigned s_arrived;
+  const int tid = threadIdx.x;
+  const int R = a.bs << a.lw;
+  const int64_t row0 = u * (int64_t)R;
+  const int q0 = (g * a.gsteps) << a.lw, q1 = min(R, ((g + 1) * a.gsteps) << a.lw), nq = q1 - q0;
+  // 1'. this block's rows: offsets (relative to row q0) and right-hand sides
+  const int32_t *xg = a.x_rel + u * a.x_stride + q0;
+  for (int k = tid; k <= nq; k += NT) xr[k] = xg[k];
+  for (int k = tid; k < nq; k += NT) ts[k] = (T)in[row0 + q0 + k];
+  const int64_t xbeg = a.x_ptr[u];
+  __syncthreads();
+  // 2'.-3'. as phases 2-3, over groups of this block's rows
+  for (int k0 = 0; k0 < nq;) {
+    const int k1 = rows_fitting(xr, k0, nq, a.chunk);
+    const int e_beg = xr[k0], e_end = xr[k1];
+    for (int e0 = e_beg + tid; e0 < e_end; e0 += NT * kWideU) {
+      int32_t c[kWideU];
+      T v[kWideU], gg[kWideU];
+#pragma unroll
+      for (int k = 0; k < kWideU; ++k) {
+        const int e = e0 + k * NT;
+        if (e < e_end) {
+          c[k] = a.x_col[xbeg + e];
+          v[k] = a.x_val[xbeg + e];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kWideU; ++k)
+        if (e0 + k * NT < e_end) gg[k] = (T)gsrc[c[k]];
+#pragma unroll
+      for (int k = 0; k < kWideU; ++k) {
+        const int e = e0 + k * NT;
+        if (e < e_end) {
+          vv[e - e_beg] = v[k];
+          gv[e - e_beg] = gg[k];
+        }
+      }
+    }
+    __syncthreads();
+    for (int k = k0 + tid; k < k1; k += NT) {
+      T acc = ts[k];
+      const int pe = xr[k + 1];
+      for (int p = xr[k]; p < pe; ++p) acc = fma(-vv[p - e_beg], gv[p - e_beg], acc);
+      ts[k] = acc;
+    }
+    __syncthreads();
+    k0 = k1;
+  }
+  for (int k = tid; k < nq; k += NT) out[row0 + q0 + k] = (OUT)ts[k];
+  __threadfence();
+  __syncthreads();
+  const int ng = (a.bs + a.gsteps - 1) / a.gsteps;
+  if (tid == 0) s_arrived = atomicAdd(&a.ucnt[u], 1u);
+  __syncthreads();
+  if (s_arrived != (unsigned)(ng - 1)) return false;
+  // 1. (the level-1 block's last CUDA block) every row's sum, dinv, r, the
+  // same-block run
+  __threadfence();
+  if (tid == 0) a.ucnt[u] = 0;
+  const int32_t *rc = a.rec + u * a.rec_ints;
+  for (int k = tid; k < a.rec_ints; k += NT) rs[k] = rc[k];
+  for (int lr = tid; lr < R; lr += NT) {
+    ts[lr] = (T)__ldcg(out + row0 + lr);
+    ds[lr] = a.dinv[row0 + lr];
+    if (!FWD && dot) rr[lr] = r[row0 + lr];
   }
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
-  const double rho_new = block_sum_rt(acc);
-  if (threadIdx.x != 0) return;
-  sc->cnt[CNT_RZ] = 0;
-  sc->rho_new = rho_new;
-  if (sc->timeout) return;
-  if (!(rho_new > 0.0) || !finite(rho_new)) {
-    sc->status = ST_BREAKDOWN;
-    sc->done = 1;
-    return;
+  const int ilen = rs[1];
+  const int64_t ibeg = rec64(rs, 4);
+  for (int e = tid; e < ilen; e += NT) {
+    iv[e] = a.i_val[ibeg + e];
+    im[e] = a.i_m[ibeg + e];
   }
-  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
-  sc->rho = rho_new;
+  __syncthreads();
+  wide_chain_store<NT, FWD, T, OUT>(a, smem, row0, out, dot, rz, out32);
+  return true;
+}
+
+template <typename T, typename Y, int NT>
+__global__ void __launch_bounds__(NT)
+    k_fwd_wsplit(const WideArgs<T> a, const double *__restrict__ r, Y *y, Scalars *sc, int check_done) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (check_done && sc->done) return;
+  const int ng = (a.bs + a.gsteps - 1) / a.gsteps;
+  double rz = 0.0;
+  wsplit_unit<NT, true, T, double, Y, Y>(a, smem, a.tile0 + blockIdx.x / ng, (int)(blockIdx.x % ng), r, y, y,
+                                         nullptr, false, rz, nullptr);
+}
+
+template <typename T, typename Y, int NT>
+__global__ void __launch_bounds__(NT)
+    k_bwd_wsplit(const WideArgs<T> a, const Y *__restrict__ yin, double *z, float *z32,
+                 const double *__restrict__ r, Scalars *sc, int check_done, int dot_mode, double *part,
+                 int64_t part_off, int last_launch, int64_t part_total) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (check_done && sc->done) return;
+  const int ng = (a.bs + a.gsteps - 1) / a.gsteps;
+  double rz = 0.0;
+  const bool unit_last = wsplit_unit<NT, false, T, Y, T, double>(
+      a, smem, a.tile0 + blockIdx.x / ng, (int)(blockIdx.x % ng), yin, zgather<T>(z, z32), z, r, dot_mode != 0,
+      rz, z32);
+  if (!dot_mode || !unit_last) return;
+  // one partial per level-1 block; the launch's last one reduces
+  bwd_dot_tail(rz, sc, dot_mode, part, part_off + blockIdx.x / ng, last_launch, part_total, gridDim.x / ng);
 }
 
 uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
@@ -389,6 +528,28 @@ WidePlan plan_one(int bs, int w, bool fwd, bool tma, int rec_ints, int64_t max_o
   return p;
 }
 
+// Split form: one step per CUDA block, a staging area for about three CUDA
+// blocks per SM (more if the longest row needs it).
+constexpr size_t kSplitSmem = 72 * 1024;
+WidePlan plan_split_form(int bs, int w, bool fwd, int rec_ints, int64_t max_i, int64_t max_row, size_t tsize) {
+  WidePlan p;
+  const WidePlan z = plan_whole(bs, w, fwd, false, rec_ints, 0, max_i, tsize);
+  if (!z.ok || rec_ints > (int)kWideRecInts) return p;
+  for (size_t budget = kSplitSmem; budget <= kWideSmemBudget; budget += 32 * 1024) {
+    if (z.smem_bytes + 64 >= budget) continue;
+    const int64_t cap = (int64_t)(budget - z.smem_bytes - 64) / (int64_t)(2 * tsize) / 32 * 32;
+    if (cap < max_row || cap < 32) continue;
+    p = plan_whole(bs, w, fwd, false, rec_ints, cap, max_i, tsize);
+    p.chunk = (int32_t)cap;
+    return p;
+  }
+  return p;
+}
+
+const WidePlan &split_plan(const DeviceLayout &d, bool fwd, int prec) {
+  return prec == HBMC_PREC_F64 ? (fwd ? d.ws_f64_f : d.ws_f64_b) : (fwd ? d.ws_f32_f : d.ws_f32_b);
+}
+
 const WidePlan &wide_plan(const DeviceLayout &d, bool fwd, int prec) {
   return prec == HBMC_PREC_F64 ? (fwd ? d.wd_f64_f : d.wd_f64_b) : (fwd ? d.wd_f32_f : d.wd_f32_b);
 }
@@ -421,6 +582,8 @@ WideArgs<T> wide_args(const DeviceLayout &d, bool fwd, int c, const WidePlan &p)
   a.lw = d.lw;
   a.tile0 = d.tile_ptr[c];
   a.chunk = p.chunk;
+  a.gsteps = 1;
+  a.ucnt = d.ucnt;
   a.off_xr = p.off_xr;
   a.off_ts = p.off_ts;
   a.off_tin = p.off_tin;
@@ -452,8 +615,19 @@ void plan_wide_kernels(const HostLayout &h, DeviceLayout &d) {
       for (int64_t u = u0; u < u1; ++u) run += rec[(size_t)u * h.rec_ints];
       const bool long_runs = u1 > u0 && run >= kWideMinRun * (u1 - u0);
       pick[c] = (long_runs || u1 - u0 < 2 * (int64_t)d.sm_count) ? 1 : 0;
+      // fewer level-1 blocks than two per SM, with very long runs (rows of
+      // 80 or more entries): spread each level-1 block's gathers over bs
+      // CUDA blocks.  Measured: it wins on the structural matrix (runs of
+      // 12k-22k entries), loses on the 27-point and 3-DOF ones (5k-9k).
+      const std::vector<int64_t> &xp = dir == 0 ? h.fx_ptr : h.bx_ptr;
+      const bool very_long = u1 > u0 && xp[u1] - xp[u0] >= kSplitMinRun * (u1 - u0);
+      if (pick[c] && very_long && u1 - u0 < 2 * (int64_t)d.sm_count) pick[c] = 2;
     }
   }
+  d.ws_f64_f = plan_split_form(h.bs, h.w, true, h.rec_ints, h.max_i_f, h.max_xrow_f, 8);
+  d.ws_f64_b = plan_split_form(h.bs, h.w, false, h.rec_ints, h.max_i_b, h.max_xrow_b, 8);
+  d.ws_f32_f = plan_split_form(h.bs, h.w, true, h.rec_ints, h.max_i_f, h.max_xrow_f, 4);
+  d.ws_f32_b = plan_split_form(h.bs, h.w, false, h.rec_ints, h.max_i_b, h.max_xrow_b, 4);
   // unpadded runs: the longest level-1 block run and the longest row
   for (int tma = 0; tma < 2; ++tma) {
     (tma ? d.wt_f64_f : d.wd_f64_f) = plan_one(h.bs, h.w, true, tma, h.rec_ints, h.max_x_f, h.max_i_f, h.max_xrow_f, 8);
@@ -472,15 +646,32 @@ cudaError_t allow_nt() {
   return cudaSuccess;
 }
 
+constexpr int kSplitThreads = 256;
+
 cudaError_t setup_wide_kernels() {
   cudaError_t e;
   if ((e = allow_nt<256, false>()) || (e = allow_nt<512, false>()) || (e = allow_nt<1024, false>()) ||
       (e = allow_nt<256, true>()) || (e = allow_nt<512, true>()) || (e = allow_nt<1024, true>()))
     return e;
+  if ((e = allow(k_fwd_wsplit<double, double, kSplitThreads>)) ||
+      (e = allow(k_fwd_wsplit<float, float, kSplitThreads>)) ||
+      (e = allow(k_bwd_wsplit<double, double, kSplitThreads>)) ||
+      (e = allow(k_bwd_wsplit<float, float, kSplitThreads>)))
+    return e;
   return cudaSuccess;
 }
 
-bool wide_all(const DeviceLayout &d) { return d.sweep_kernel == 4 || d.sweep_kernel == 6; }
+bool wide_all(const DeviceLayout &d) { return d.sweep_kernel == 4 || d.sweep_kernel == 6 || d.sweep_kernel == 7; }
+
+// The split form for color c: always under sweep_kernel 7, by the per-color
+// pick under automatic selection; it needs its plan and the counters.
+static bool use_split(const DeviceLayout &d, bool fwd, int prec, int c) {
+  if (!d.ucnt || !split_plan(d, fwd, prec).ok) return false;
+  if (d.sweep_kernel == 7) return true;
+  if (d.sweep_kernel != 0) return false;
+  const std::vector<uint8_t> &v = fwd ? d.wide_f : d.wide_b;
+  return c < (int)v.size() && v[c] == 2;
+}
 
 bool wide_usable(const DeviceLayout &d, bool fwd, int prec) {
   return (d.sweep_kernel == 0 || wide_all(d)) && d.rec_f && wide_plan(d, fwd, prec).ok;
@@ -560,6 +751,17 @@ static bool wide_use_tma(const DeviceLayout &d, bool fwd, int prec, int c) {
 void launch_fwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done,
                            cudaStream_t s) {
   if (wide_color_grid(d, c) == 0) return;
+  if (use_split(d, true, prec, c)) {
+    const WidePlan &p = split_plan(d, true, prec);
+    const unsigned grid = wide_color_grid(d, c) * (unsigned)d.bs;
+    if (prec == HBMC_PREC_F64)
+      k_fwd_wsplit<double, double, kSplitThreads><<<grid, kSplitThreads, p.smem_bytes, s>>>(
+          wide_args<double>(d, true, c, p), r, d.y, d.sc, check_done ? 1 : 0);
+    else
+      k_fwd_wsplit<float, float, kSplitThreads><<<grid, kSplitThreads, p.smem_bytes, s>>>(
+          wide_args<float>(d, true, c, p), r, d.y32, d.sc, check_done ? 1 : 0);
+    return;
+  }
   const WidePlan &pt = wide_tma_plan(d, true, prec);
   const bool tma = wide_use_tma(d, true, prec, c);
   const WidePlan &p = tma ? pt : wide_plan(d, true, prec);
@@ -575,6 +777,19 @@ void launch_fwd_wide_color(const DeviceLayout &d, int prec, int c, const double 
 void launch_bwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
                            int64_t part_off, bool last, int64_t part_total, cudaStream_t s) {
   if (wide_color_grid(d, c) == 0) return;
+  if (use_split(d, false, prec, c)) {
+    const WidePlan &p = split_plan(d, false, prec);
+    const unsigned grid = wide_color_grid(d, c) * (unsigned)d.bs;
+    if (prec == HBMC_PREC_F64)
+      k_bwd_wsplit<double, double, kSplitThreads><<<grid, kSplitThreads, p.smem_bytes, s>>>(
+          wide_args<double>(d, false, c, p), d.y, d.z, d.z32, r, d.sc, check_done ? 1 : 0, dot_mode, d.part,
+          part_off, last ? 1 : 0, part_total);
+    else
+      k_bwd_wsplit<float, float, kSplitThreads><<<grid, kSplitThreads, p.smem_bytes, s>>>(
+          wide_args<float>(d, false, c, p), d.y32, d.z, d.z32, r, d.sc, check_done ? 1 : 0, dot_mode, d.part,
+          part_off, last ? 1 : 0, part_total);
+    return;
+  }
   const WidePlan &pt = wide_tma_plan(d, false, prec);
   const bool tma = wide_use_tma(d, false, prec, c);
   const WidePlan &p = tma ? pt : wide_plan(d, false, prec);

@@ -357,10 +357,11 @@ def test_sweep_kernel_variants_agree(lib, orc, name, mk, bs, w, box, precision):
     small colors), 1 block per level-1 block, 2 TMA-fed persistent, 3 warp
     per level-1 block with plain loads, 4 loader-thread blocks staged by bulk
     copy, 5 warp per level-1 block staged by bulk copy (bs 4 and 8), 6
-    loader-thread blocks with plain loads."""
+    loader-thread blocks with plain loads, 7 loader-thread sweeps split over
+    bs CUDA blocks per level-1 block."""
     A = mk()
     outs = []
-    for sk in (0, 1, 2, 3, 4, 5, 6):
+    for sk in (0, 1, 2, 3, 4, 5, 6, 7):
         ctx = H.hbmc_build(A, bs, w, box=box, sweep_kernel=sk, precision=precision)
         assert H.hbmc_ic0(ctx, 0.1)[0] == H.OK
         n_pad = ctx.info()["n_pad"]
