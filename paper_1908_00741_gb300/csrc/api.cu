@@ -173,20 +173,27 @@ hbmc_status upload(hbmc_ctx *ctx) {
   TRY(dalloc(ctx, d.ldiag, h.n_pad));
   TRY(dupload(ctx, d.lmap_f, h.lmap_f));
   TRY(dupload(ctx, d.lmap_b, h.lmap_b));
-  TRY(dupload(ctx, d.fx_ptr, h.fx_ptr));
-  TRY(dupload(ctx, d.bx_ptr, h.bx_ptr));
-  TRY(dupload(ctx, d.fx_rel, h.fx_rel));
-  TRY(dupload(ctx, d.bx_rel, h.bx_rel));
-  TRY(dupload(ctx, d.fx_col, h.fx_col));
-  TRY(dupload(ctx, d.bx_col, h.bx_col));
-  TRY(dupload(ctx, d.lmapx_f, h.lmapx_f));
-  TRY(dupload(ctx, d.lmapx_b, h.lmapx_b));
-  TRY(dalloc(ctx, d.ucnt, (size_t)std::max<int64_t>(h.ntiles, 1)));
-  CK(cudaMemset(d.ucnt, 0, sizeof(unsigned) * (size_t)std::max<int64_t>(h.ntiles, 1)));
-  TRY(dalloc(ctx, d.fx_val, h.fx_col.size()));
-  TRY(dalloc(ctx, d.bx_val, h.bx_col.size()));
-  TRY(dalloc(ctx, d.fx_val32, h.fx_col.size()));
-  TRY(dalloc(ctx, d.bx_val32, h.bx_col.size()));
+  // unpadded runs of the loader-thread sweeps: only layouts that carry them
+  // (the batched solver's merged layout does not; its pointers stay null and
+  // the scatter and the sweeps then skip them)
+  const bool have_x = h.fx_ptr.size() == (size_t)h.ntiles + 1 && h.bx_ptr.size() == (size_t)h.ntiles + 1 &&
+                      h.lmapx_f.size() == (size_t)h.nnz_lower && h.lmapx_b.size() == (size_t)h.nnz_lower &&
+                      h.nnz_lower > 0;
+  if (have_x) {
+    TRY(dupload(ctx, d.fx_ptr, h.fx_ptr));
+    TRY(dupload(ctx, d.bx_ptr, h.bx_ptr));
+    TRY(dupload(ctx, d.fx_rel, h.fx_rel));
+    TRY(dupload(ctx, d.bx_rel, h.bx_rel));
+    TRY(dupload(ctx, d.fx_col, h.fx_col));
+    TRY(dupload(ctx, d.bx_col, h.bx_col));
+    TRY(dupload(ctx, d.lmapx_f, h.lmapx_f));
+    TRY(dupload(ctx, d.lmapx_b, h.lmapx_b));
+    TRY(dalloc(ctx, d.fx_val, h.fx_col.size()));
+    TRY(dalloc(ctx, d.bx_val, h.bx_col.size()));
+    TRY(dalloc(ctx, d.fx_val32, h.fx_col.size()));
+    TRY(dalloc(ctx, d.bx_val32, h.bx_col.size()));
+    TRY(dalloc(ctx, d.ucnt, (size_t)std::max<int64_t>(h.ntiles, 1)));
+  }
   const size_t nv = (size_t)(h.n_pad + hbmc::kGuard);
   TRY(dalloc(ctx, d.b, nv));
   TRY(dalloc(ctx, d.x, nv));

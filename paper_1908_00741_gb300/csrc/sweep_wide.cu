@@ -605,6 +605,15 @@ cudaError_t allow(K kernel) {
 }  // namespace
 
 void plan_wide_kernels(const HostLayout &h, DeviceLayout &d) {
+  // Layouts without the unpadded runs (the batched solver's merged layout)
+  // leave every plan unusable and every color on the warp kernels.
+  const size_t nx = (size_t)h.ntiles + 1;
+  if (h.fx_ptr.size() != nx || h.bx_ptr.size() != nx || h.rec_f.empty() || h.rec_b.empty() || !d.fx_ptr ||
+      !d.bx_ptr || !d.ucnt) {
+    d.wide_f.assign(h.nc, 0);
+    d.wide_b.assign(h.nc, 0);
+    return;
+  }
   for (int dir = 0; dir < 2; ++dir) {
     const std::vector<int32_t> &rec = dir == 0 ? h.rec_f : h.rec_b;
     std::vector<uint8_t> &pick = dir == 0 ? d.wide_f : d.wide_b;
