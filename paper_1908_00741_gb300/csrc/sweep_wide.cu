@@ -54,6 +54,7 @@ constexpr uint64_t kWideWaitNs = 4000000000ull;
 constexpr int64_t kWideMinRun = 2048;
 // ... and their split form when the unpadded runs average this many entries.
 constexpr int64_t kSplitMinRun = 12288;
+constexpr int kSplitU = 16;  // split form: entries per thread and trip (256 threads: 4096 a trip)
 
 template <typename T>
 struct WideArgs {
@@ -377,21 +378,26 @@ __device__ __forceinline__ bool wsplit_unit(const WideArgs<T> &a, unsigned char 
   const int R = a.bs << a.lw;
   const int64_t row0 = u * (int64_t)R;
   const int q0 = (g * a.gsteps) << a.lw, q1 = min(R, ((g + 1) * a.gsteps) << a.lw), nq = q1 - q0;
-  // 1'. this block's rows: offsets (relative to row q0) and right-hand sides
+  // 1'. this block's rows: offsets (relative to row q0) and right-hand
+  // sides; the record too, so that a last block can fetch the same-block run
+  // together with the sums
   const int32_t *xg = a.x_rel + u * a.x_stride + q0;
   for (int k = tid; k <= nq; k += NT) xr[k] = xg[k];
   for (int k = tid; k < nq; k += NT) ts[k] = (T)in[row0 + q0 + k];
+  const int32_t *rc = a.rec + u * a.rec_ints;
+  for (int k = tid; k < a.rec_ints; k += NT) rs[k] = rc[k];
   const int64_t xbeg = a.x_ptr[u];
   __syncthreads();
-  // 2'.-3'. as phases 2-3, over groups of this block's rows
+  // 2'.-3'. as phases 2-3, over groups of this block's rows, kSplitU
+  // entries per thread and trip to memory
   for (int k0 = 0; k0 < nq;) {
     const int k1 = rows_fitting(xr, k0, nq, a.chunk);
     const int e_beg = xr[k0], e_end = xr[k1];
-    for (int e0 = e_beg + tid; e0 < e_end; e0 += NT * kWideU) {
-      int32_t c[kWideU];
-      T v[kWideU], gg[kWideU];
+    for (int e0 = e_beg + tid; e0 < e_end; e0 += NT * kSplitU) {
+      int32_t c[kSplitU];
+      T v[kSplitU], gg[kSplitU];
 #pragma unroll
-      for (int k = 0; k < kWideU; ++k) {
+      for (int k = 0; k < kSplitU; ++k) {
         const int e = e0 + k * NT;
         if (e < e_end) {
           c[k] = a.x_col[xbeg + e];
@@ -399,10 +405,10 @@ __device__ __forceinline__ bool wsplit_unit(const WideArgs<T> &a, unsigned char 
         }
       }
 #pragma unroll
-      for (int k = 0; k < kWideU; ++k)
+      for (int k = 0; k < kSplitU; ++k)
         if (e0 + k * NT < e_end) gg[k] = (T)gsrc[c[k]];
 #pragma unroll
-      for (int k = 0; k < kWideU; ++k) {
+      for (int k = 0; k < kSplitU; ++k) {
         const int e = e0 + k * NT;
         if (e < e_end) {
           vv[e - e_beg] = v[k];
@@ -427,20 +433,17 @@ __device__ __forceinline__ bool wsplit_unit(const WideArgs<T> &a, unsigned char 
   if (tid == 0) s_arrived = atomicAdd(&a.ucnt[u], 1u);
   __syncthreads();
   if (s_arrived != (unsigned)(ng - 1)) return false;
-  // 1. (the level-1 block's last CUDA block) every row's sum, dinv, r, the
-  // same-block run
+  // 1. (the level-1 block's last CUDA block) every row's sum, dinv, r and the
+  // same-block run, in one trip to memory
   __threadfence();
   if (tid == 0) a.ucnt[u] = 0;
-  const int32_t *rc = a.rec + u * a.rec_ints;
-  for (int k = tid; k < a.rec_ints; k += NT) rs[k] = rc[k];
+  const int ilen = rs[1];
+  const int64_t ibeg = rec64(rs, 4);
   for (int lr = tid; lr < R; lr += NT) {
     ts[lr] = (T)__ldcg(out + row0 + lr);
     ds[lr] = a.dinv[row0 + lr];
     if (!FWD && dot) rr[lr] = r[row0 + lr];
   }
-  __syncthreads();
-  const int ilen = rs[1];
-  const int64_t ibeg = rec64(rs, 4);
   for (int e = tid; e < ilen; e += NT) {
     iv[e] = a.i_val[ibeg + e];
     im[e] = a.i_m[ibeg + e];
@@ -451,7 +454,7 @@ __device__ __forceinline__ bool wsplit_unit(const WideArgs<T> &a, unsigned char 
 }
 
 template <typename T, typename Y, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 2)
     k_fwd_wsplit(const WideArgs<T> a, const double *__restrict__ r, Y *y, Scalars *sc, int check_done) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (check_done && sc->done) return;
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(NT)
 }
 
 template <typename T, typename Y, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 2)
     k_bwd_wsplit(const WideArgs<T> a, const Y *__restrict__ yin, double *z, float *z32,
                  const double *__restrict__ r, Scalars *sc, int check_done, int dot_mode, double *part,
                  int64_t part_off, int last_launch, int64_t part_total) {
