@@ -382,14 +382,16 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
     // mode it is enqueued in groups of check_every.
     // BiCGStab: init = 2 gathers, residual, start; per iteration 7 kernels
     // and two preconditioner applications (4 n_c sweeps).
-    // Row-split SpMV: one more launch for the pieces.
-    const int64_t nc = d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc + (d.split && d.n_virt > 0 ? 1 : 0);
+    // Row-split SpMV: one more launch for the pieces; the fused last color
+    // of the preconditioner: one launch fewer.
+    const int64_t fb = !bicg && hbmc::fb_tw_usable(d, prec) ? 1 : 0;
+    const int64_t nc = d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc + (d.split && d.n_virt > 0 ? 1 : 0) - fb;
     int64_t passes = r.iters > 0 ? r.iters : 1;
     if (ctx->opt.loop_mode == HBMC_LOOP_HOST) {
       const int64_t every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
       passes = (passes + every - 1) / every * every;
     }
-    ctx->last_launches = persistent ? 5 : (bicg ? 4 : 4 + 2 * nc) + passes * per + 2;
+    ctx->last_launches = persistent ? 5 : (bicg ? 4 : 4 + 2 * nc - fb) + passes * per + 2;
   }
   if (iters) *iters = r.iters;
   if (relres) *relres = r.relres;
@@ -689,8 +691,7 @@ hbmc_status hbmc_precond(hbmc_ctx *ctx, const double *r_dev, double *z_dev) {
   DeviceGuard guard(ctx->device);
   const DeviceLayout &d = ctx->d;
   hbmc::enqueue_gather_in(d, r_dev, d.r, -1, ctx->stream);
-  hbmc::enqueue_fwd(d, ctx->precision, d.r, false, ctx->stream);
-  hbmc::enqueue_bwd(d, ctx->precision, d.r, 0, false, ctx->stream);
+  hbmc::enqueue_precond(d, ctx->precision, d.r, 0, false, ctx->stream);
   hbmc::enqueue_gather_out(d, d.z, z_dev, false, ctx->stream);
   CK(cudaGetLastError());
   return HBMC_OK;

@@ -228,6 +228,7 @@ struct DeviceLayout {
   int64_t max_i_f = 0, max_i_b = 0;
   WarpPlan wp_f64_f, wp_f64_b, wp_f32_f, wp_f32_b, wp_spmv;
   TwPlan tw_f64_f, tw_f64_b, tw_f32_f, tw_f32_b;
+  TwPlan tw_fb_f64, tw_fb_f32;  // last color, forward and backward in one pass
   SpmvPlan sp;
   SorPlan sor;
   WidePlan wd_f64_f, wd_f64_b, wd_f32_f, wd_f32_b;  // plain-load staging

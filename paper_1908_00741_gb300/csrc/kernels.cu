@@ -760,6 +760,39 @@ void enqueue_relres(const DeviceLayout &d, cudaStream_t s) {
       d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, d.b, d.x, d.r, d.part, d.sc, d.hist);
 }
 
+// z = M^{-1} r: the forward sweep over colors 1..n_c, then the backward
+// sweep over n_c..1 (dot_mode as enqueue_bwd).  When the last color runs on
+// the bulk-copy warp kernels in both directions, its forward and backward
+// passes are one launch (k_fb_tw), with the same bits.
+void enqueue_precond(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                     cudaStream_t s) {
+  if (!fb_tw_usable(d, prec)) {
+    enqueue_fwd(d, prec, r, check_done, s);
+    enqueue_bwd(d, prec, r, dot_mode, check_done, s);
+    return;
+  }
+  const bool wide_f = wide_usable(d, true, prec), wide_b = wide_usable(d, false, prec);
+  for (int c = 0; c < d.nc - 1; ++c) {
+    if (wide_f && wide_preferred(d, true, c)) launch_fwd_wide_color(d, prec, c, r, check_done, s);
+    else launch_fwd_tw_color(d, prec, c, r, check_done, s);
+  }
+  auto use_wide = [&](int c) { return wide_b && wide_preferred(d, false, c); };
+  int64_t total = 0;
+  for (int c = 0; c < d.nc; ++c) total += use_wide(c) ? wide_color_grid(d, c) : tw_color_grid(d, c);
+  int64_t off = 0;
+  launch_fb_tw_last(d, prec, r, dot_mode, check_done, off, d.nc == 1, total, s);
+  off += tw_color_grid(d, d.nc - 1);
+  for (int c = d.nc - 2; c >= 0; --c) {
+    if (use_wide(c)) {
+      launch_bwd_wide_color(d, prec, c, r, dot_mode, check_done, off, c == 0, total, s);
+      off += wide_color_grid(d, c);
+    } else {
+      launch_bwd_tw_color(d, prec, c, r, dot_mode, check_done, off, c == 0, total, s);
+      off += tw_color_grid(d, c);
+    }
+  }
+}
+
 // Before the loop: permute b and x0 in, r = b - A x, ||b||, z = M^{-1} r,
 // rho = r.z, p = z.
 void enqueue_init(const DeviceLayout &d, int prec, cudaStream_t s) {
@@ -767,8 +800,7 @@ void enqueue_init(const DeviceLayout &d, int prec, cudaStream_t s) {
   enqueue_gather_in(d, nullptr, d.x, 1, s);
   k_residual<0><<<row_grid(d), kRowThreads, 0, s>>>(
       d.a_ptr, d.a_col, d.a_val, d.w, d.lw, d.n_pad, d.b, d.x, d.r, d.part, d.sc, d.hist);
-  enqueue_fwd(d, prec, d.r, true, s);
-  enqueue_bwd(d, prec, d.r, 1, true, s);
+  enqueue_precond(d, prec, d.r, 1, true, s);
   k_update_p<<<row_grid(d), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 0, 0, 0);
 }
 
@@ -778,8 +810,7 @@ void enqueue_body(const DeviceLayout &d, int prec, cudaStream_t s, bool use_cond
   enqueue_spmv(d, d.p, d.q, true, s);
   k_update_xr<<<row_grid(d), kRowThreads, 0, s>>>(
       d.n_pad, d.p, d.q, d.x, d.r, d.part, d.sc, d.hist, use_cond ? 1 : 0, h);
-  enqueue_fwd(d, prec, d.r, true, s);
-  enqueue_bwd(d, prec, d.r, 2, true, s);
+  enqueue_precond(d, prec, d.r, 2, true, s);
   k_update_p<<<row_grid(d), kRowThreads, 0, s>>>(d.n_pad, d.z, d.p, d.sc, 1, use_cond ? 1 : 0, h);
 }
 

@@ -30,6 +30,11 @@ cudaError_t setup_tw_kernels();
 bool tw_usable(const DeviceLayout &d, bool fwd, int prec);
 int64_t tw_partials_needed(const DeviceLayout &d);
 unsigned tw_color_grid(const DeviceLayout &d, int c);
+bool fb_tw_usable(const DeviceLayout &d, int prec);
+void launch_fb_tw_last(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                       int64_t part_off, bool last, int64_t part_total, cudaStream_t s);
+void enqueue_precond(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                     cudaStream_t s);
 void launch_fwd_tw_color(const DeviceLayout &d, int prec, int c, const double *r, bool check_done, cudaStream_t s);
 void launch_bwd_tw_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
                          int64_t part_off, bool last, int64_t part_total, cudaStream_t s);

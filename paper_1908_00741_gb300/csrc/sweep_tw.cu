@@ -168,32 +168,145 @@ __global__ void __launch_bounds__(32 * kTwWarps, kTwMinBlocks)
     tw_unit<BS, false, T, Y, T, double>(a, smem + (size_t)warp * a.warp_bytes, lane, u, yin, zgather<T>(z, z32), z,
                                         r, dot_mode != 0, rz, sc, z32);
   if (!dot_mode) return;
-  const double v = block_sum_rt(rz);
-  if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
-  if (!last_launch) return;
-  __shared__ unsigned s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
-    s_last = (t == gridDim.x - 1);
+  rz_partial(rz, sc, dot_mode, part, part_off + blockIdx.x, last_launch, part_total, gridDim.x);
+}
+
+// The last color's forward sweep and the backward sweep's first color
+// (the same color) in one pass: for the last color the backward sweep needs
+// only the unit's own y (a last color has no later colors to gather from),
+// so the warp that finishes the forward chain of a unit runs its backward
+// chain at once, and y never goes to memory.  The backward same-block run
+// reuses the forward one's shared memory: it is fetched by bulk copy once the
+// forward chain is done (a third trip, instead of a second launch).  Every
+// operation is the one the separate sweeps perform, in the same order.
+template <int BS, typename T, typename Y>
+__device__ __forceinline__ void fb_unit(const TwArgs<T> &af, const TwArgs<T> &ab, unsigned char *ws, int lane,
+                                        int64_t u, const double *r, const Y *ysrc, double *z, float *z32, bool dot,
+                                        double &rz, Scalars *sc) {
+  constexpr uint32_t R = (uint32_t)BS * 32;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(ws);
+  int32_t *rs = reinterpret_cast<int32_t *>(ws + kRecOff);
+  T *ts = reinterpret_cast<T *>(ws + af.off_ts);
+  double *tin = reinterpret_cast<double *>(ws + af.off_tin);  // == ts in FP64
+  T *ds = reinterpret_cast<T *>(ws + af.off_ds);
+  T *iv = reinterpret_cast<T *>(ws + af.off_iv);
+  uint8_t *im = ws + af.off_im;
+  const int64_t row0 = u * (int64_t)R;
+  // trip 1: r and dinv (dinv is the same array in both directions for IC(0))
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    mbar_expect_tx(bar, R * (uint32_t)(sizeof(double) + sizeof(T)));
+    tma_load_1d(tin, r + row0, R * 8u, bar);
+    tma_load_1d(ds, af.dinv + row0, R * (uint32_t)sizeof(T), bar);
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
-  const double rho_new = block_sum_rt(acc);
-  if (threadIdx.x != 0) return;
-  sc->cnt[CNT_RZ] = 0;
-  sc->rho_new = rho_new;
-  if (sc->timeout) return;
-  if (!(rho_new > 0.0) || !finite(rho_new)) {
-    sc->status = ST_BREAKDOWN;
-    sc->done = 1;
+  const int32_t *rcf = af.rec + u * af.rec_ints, *rcb = ab.rec + u * ab.rec_ints;
+  const int32_t f0 = lane < af.rec_ints ? rcf[lane] : 0, f1 = lane + 32 < af.rec_ints ? rcf[lane + 32] : 0;
+  const int32_t b0 = lane < ab.rec_ints ? rcb[lane] : 0, b1 = lane + 32 < ab.rec_ints ? rcb[lane + 32] : 0;
+  const int olen = rec_at(f0, f1, 0), ilen = rec_at(f0, f1, 1);
+  const int64_t obeg = (int64_t)(((uint64_t)(uint32_t)rec_at(f0, f1, 3) << 32) | (uint32_t)rec_at(f0, f1, 2));
+  const int64_t ibeg = (int64_t)(((uint64_t)(uint32_t)rec_at(f0, f1, 5) << 32) | (uint32_t)rec_at(f0, f1, 4));
+  const int olen_b = rec_at(b0, b1, 0), ilen_b = rec_at(b0, b1, 1);
+  const int64_t obeg_b = (int64_t)(((uint64_t)(uint32_t)rec_at(b0, b1, 3) << 32) | (uint32_t)rec_at(b0, b1, 2));
+  const int64_t ibeg_b = (int64_t)(((uint64_t)(uint32_t)rec_at(b0, b1, 5) << 32) | (uint32_t)rec_at(b0, b1, 4));
+  // trip 2: the forward same-block run
+  if (lane == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)ilen * (uint32_t)(sizeof(T) + 1));
+    if (ilen > 0) {
+      tma_load_1d(iv, af.i_val + ibeg, (uint32_t)ilen * (uint32_t)sizeof(T), bar);
+      tma_load_1d(im, af.i_m + ibeg, (uint32_t)ilen, bar);
+    }
+  }
+  if (lane < af.rec_ints) rs[lane] = f0;
+  if (lane + 32 < af.rec_ints) rs[lane + 32] = f1;
+  __syncwarp();
+  const uint64_t deadline = global_ns() + kTwWaitNs;
+  if (!__all_sync(0xffffffffu, mbar_wait(bar, 0, deadline))) {
+    if (lane == 0) {
+      sc->timeout = 1;
+      sc->done = 1;
+    }
+    mbar_wait(bar, 0, deadline + kTwWaitNs);  // let the copies land before the warp leaves
     return;
   }
-  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
-  sc->rho = rho_new;
+  if constexpr (!std::is_same<T, double>::value) {
+#pragma unroll
+    for (int l = 0; l < BS; ++l) ts[(l << 5) + lane] = (T)tin[(l << 5) + lane];
+  }
+  run_accumulate<T, Y, true>(af.o_col, af.o_val, ysrc, obeg, olen, rs + 6, ts, lane);
+  {
+    const int32_t *i_rel = rs + 7 + BS;
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+      T acc = ts[(q << 5) + lane];
+      const int pe = i_rel[q + 1];
+      for (int p = i_rel[q] + lane; p < pe; p += 32) acc = fma(-iv[p], ts[(im[p] << 5) + lane], acc);
+      ts[(q << 5) + lane] = acc * ds[(q << 5) + lane];
+    }
+  }
+  // trip 3: the backward same-block run into the same buffers, the backward
+  // record into rs
+  __syncwarp();
+  if (lane == 0) {
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, (uint32_t)ilen_b * (uint32_t)(sizeof(T) + 1));
+    if (ilen_b > 0) {
+      tma_load_1d(iv, ab.i_val + ibeg_b, (uint32_t)ilen_b * (uint32_t)sizeof(T), bar);
+      tma_load_1d(im, ab.i_m + ibeg_b, (uint32_t)ilen_b, bar);
+    }
+  }
+  if (lane < ab.rec_ints) rs[lane] = b0;
+  if (lane + 32 < ab.rec_ints) rs[lane + 32] = b1;
+  double rv[BS];
+  if (dot) {
+#pragma unroll
+    for (int q = 0; q < BS; ++q) rv[q] = r[row0 + (q << 5) + lane];
+  }
+  __syncwarp();
+  // a last color has no later colors: its backward other-color run is empty
+  run_accumulate<T, T, true>(ab.o_col, ab.o_val, zgather<T>(z, z32), obeg_b, olen_b, rs + 6, ts, lane);
+  if (!__all_sync(0xffffffffu, mbar_wait(bar, 1, deadline + kTwWaitNs))) {
+    if (lane == 0) {
+      sc->timeout = 1;
+      sc->done = 1;
+    }
+    mbar_wait(bar, 1, deadline + 2 * kTwWaitNs);
+    return;
+  }
+  {
+    const int32_t *i_rel = rs + 7 + BS;
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+      const int lq = BS - 1 - q;
+      T acc = ts[(lq << 5) + lane];
+      const int pe = i_rel[lq + 1];
+      for (int p = i_rel[lq] + lane; p < pe; p += 32) acc = fma(-iv[p], ts[(im[p] << 5) + lane], acc);
+      ts[(lq << 5) + lane] = acc * ds[(lq << 5) + lane];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    const T zv = ts[(q << 5) + lane];
+    z[row0 + (q << 5) + lane] = (double)zv;
+    if constexpr (sizeof(T) == 4) z32[row0 + (q << 5) + lane] = zv;
+    if (dot) rz = fma(rv[q], (double)zv, rz);
+  }
+}
+
+template <typename T, typename Y, int BS>
+__global__ void __launch_bounds__(32 * kTwWarps, kTwMinBlocks)
+    k_fb_tw(const TwArgs<T> af, const TwArgs<T> ab, const double *__restrict__ r, const Y *ysrc, double *z,
+            float *z32, Scalars *sc, int check_done, int dot_mode, double *part, int64_t part_off, int last_launch,
+            int64_t part_total) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (check_done && sc->done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = af.tile0 + (int64_t)blockIdx.x * kTwWarps + warp;
+  double rz = 0.0;
+  if (u < af.tile0 + af.ntiles)
+    fb_unit<BS, T, Y>(af, ab, smem + (size_t)warp * af.warp_bytes, lane, u, r, ysrc, z, z32, dot_mode != 0, rz, sc);
+  if (!dot_mode) return;
+  rz_partial(rz, sc, dot_mode, part, part_off + blockIdx.x, last_launch, part_total, gridDim.x);
 }
 
 uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
@@ -281,6 +394,44 @@ void plan_tw_kernels(const HostLayout &h, DeviceLayout &d) {
   d.tw_f64_b = plan_one(h.bs, false, h.rec_ints, h.max_i_b, 8);
   d.tw_f32_f = plan_one(h.bs, true, h.rec_ints, h.max_i_f, 4);
   d.tw_f32_b = plan_one(h.bs, false, h.rec_ints, h.max_i_b, 4);
+  // the same-block buffers hold either direction's run
+  const int64_t mi = std::max(h.max_i_f, h.max_i_b);
+  d.tw_fb_f64 = plan_one(h.bs, true, h.rec_ints, mi, 8);
+  d.tw_fb_f32 = plan_one(h.bs, true, h.rec_ints, mi, 4);
+}
+
+// The fused last-color pass: both directions on the bulk-copy warp kernels
+// for the last color, one dinv for both (IC(0)), and its plan fits.
+bool fb_tw_usable(const DeviceLayout &d, int prec) {
+  if (d.nc < 1 || !tw_usable(d, true, prec) || !tw_usable(d, false, prec)) return false;
+  if (d.dinvb != d.dinv || d.dinvb32 != d.dinv32) return false;
+  const int c = d.nc - 1;
+  if (wide_usable(d, true, prec) && wide_preferred(d, true, c)) return false;
+  if (wide_usable(d, false, prec) && wide_preferred(d, false, c)) return false;
+  return (prec == HBMC_PREC_F64 ? d.tw_fb_f64 : d.tw_fb_f32).ok;
+}
+
+template <typename T, typename Y, int BS>
+static void launch_fb(const DeviceLayout &d, const double *r, const Y *ysrc, int dot_mode, bool check_done,
+                      int64_t part_off, bool last, int64_t part_total, cudaStream_t s) {
+  const int c = d.nc - 1;
+  const TwPlan &pf = sizeof(T) == 8 ? d.tw_fb_f64 : d.tw_fb_f32;
+  const TwPlan &pb = sizeof(T) == 8 ? d.tw_f64_b : d.tw_f32_b;
+  k_fb_tw<T, Y, BS><<<tw_grid(d, c), 32 * kTwWarps, (size_t)kTwWarps * pf.warp_bytes, s>>>(
+      tw_args<T>(d, true, c, pf), tw_args<T>(d, false, c, pb), r, ysrc, d.z, d.z32, d.sc, check_done ? 1 : 0,
+      dot_mode, d.part, part_off, last ? 1 : 0, part_total);
+}
+
+void launch_fb_tw_last(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                       int64_t part_off, bool last, int64_t part_total, cudaStream_t s) {
+  if (tw_color_grid(d, d.nc - 1) == 0) return;
+  if (prec == HBMC_PREC_F64) {
+    if (d.bs == 8) launch_fb<double, double, 8>(d, r, d.y, dot_mode, check_done, part_off, last, part_total, s);
+    else launch_fb<double, double, 4>(d, r, d.y, dot_mode, check_done, part_off, last, part_total, s);
+  } else {
+    if (d.bs == 8) launch_fb<float, float, 8>(d, r, d.y32, dot_mode, check_done, part_off, last, part_total, s);
+    else launch_fb<float, float, 4>(d, r, d.y32, dot_mode, check_done, part_off, last, part_total, s);
+  }
 }
 
 cudaError_t setup_tw_kernels() {
@@ -288,7 +439,9 @@ cudaError_t setup_tw_kernels() {
   if ((e = allow(k_fwd_tw<double, double, 4>)) || (e = allow(k_fwd_tw<double, double, 8>)) ||
       (e = allow(k_fwd_tw<float, float, 4>)) || (e = allow(k_fwd_tw<float, float, 8>)) ||
       (e = allow(k_bwd_tw<double, double, 4>)) || (e = allow(k_bwd_tw<double, double, 8>)) ||
-      (e = allow(k_bwd_tw<float, float, 4>)) || (e = allow(k_bwd_tw<float, float, 8>)))
+      (e = allow(k_bwd_tw<float, float, 4>)) || (e = allow(k_bwd_tw<float, float, 8>)) ||
+      (e = allow(k_fb_tw<double, double, 4>)) || (e = allow(k_fb_tw<double, double, 8>)) ||
+      (e = allow(k_fb_tw<float, float, 4>)) || (e = allow(k_fb_tw<float, float, 8>)))
     return e;
   return cudaSuccess;
 }

@@ -289,39 +289,6 @@ __device__ __forceinline__ bool wide_unit_tma(const WideArgs<T> &a, unsigned cha
   return true;
 }
 
-// r.z of a backward sweep: this CUDA block's partial into part[slot]; in
-// the last launch of the sweep, the last of its `nparts` contributing blocks
-// adds every partial of the sweep (part_total) in index order.
-__device__ __forceinline__ void bwd_dot_tail(double rz, Scalars *sc, int dot_mode, double *part, int64_t slot,
-                                             int last_launch, int64_t part_total, unsigned nparts) {
-  const double v = block_sum_rt(rz);
-  if (threadIdx.x == 0) part[slot] = v;
-  if (!last_launch) return;
-  __shared__ unsigned s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
-    s_last = (t == nparts - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
-  const double rho_new = block_sum_rt(acc);
-  if (threadIdx.x != 0) return;
-  sc->cnt[CNT_RZ] = 0;
-  sc->rho_new = rho_new;
-  if (sc->timeout) return;
-  if (!(rho_new > 0.0) || !finite(rho_new)) {
-    sc->status = ST_BREAKDOWN;
-    sc->done = 1;
-    return;
-  }
-  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
-  sc->rho = rho_new;
-}
-
 template <typename T, typename Y, int NT, bool TMA>
 __global__ void __launch_bounds__(NT)
     k_fwd_wide(const WideArgs<T> a, const double *__restrict__ r, Y *y, Scalars *sc, int check_done) {
@@ -349,7 +316,7 @@ __global__ void __launch_bounds__(NT)
     wide_unit<NT, false, T, Y, T, double>(a, smem, a.tile0 + blockIdx.x, yin, zgather<T>(z, z32), z, r,
                                           dot_mode != 0, rz, z32);
   if (!dot_mode) return;
-  bwd_dot_tail(rz, sc, dot_mode, part, part_off + blockIdx.x, last_launch, part_total, gridDim.x);
+  rz_partial(rz, sc, dot_mode, part, part_off + blockIdx.x, last_launch, part_total, gridDim.x);
 }
 
 // Split variant (colors with few, long level-1 blocks): CUDA block b works
@@ -478,7 +445,7 @@ __global__ void __launch_bounds__(NT, 2)
       rz, z32);
   if (!dot_mode || !unit_last) return;
   // one partial per level-1 block; the launch's last one reduces
-  bwd_dot_tail(rz, sc, dot_mode, part, part_off + blockIdx.x / ng, last_launch, part_total, gridDim.x / ng);
+  rz_partial(rz, sc, dot_mode, part, part_off + blockIdx.x / ng, last_launch, part_total, gridDim.x / ng);
 }
 
 uint32_t a16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }

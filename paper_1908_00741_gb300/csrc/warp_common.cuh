@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "device_util.cuh"
+#include "hbmc_internal.h"
 
 namespace hbmc {
 
@@ -66,6 +67,40 @@ __device__ __forceinline__ void run_accumulate(const int32_t *__restrict__ col, 
       }
     }
   }
+}
+
+// r.z of a backward sweep: this CUDA block's partial into part[slot]; in
+// the sweep's last launch, the last of its `nparts` contributing blocks adds
+// every partial of the sweep (part_total) in index order and takes the CG
+// scalars' step (dot_mode 1: rho; 2: rho and beta).
+__device__ __forceinline__ void rz_partial(double rz, Scalars *sc, int dot_mode, double *part, int64_t slot,
+                                           int last_launch, int64_t part_total, unsigned nparts) {
+  const double v = block_sum_rt(rz);
+  if (threadIdx.x == 0) part[slot] = v;
+  if (!last_launch) return;
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
+    s_last = (t == nparts - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
+  const double rho_new = block_sum_rt(acc);
+  if (threadIdx.x != 0) return;
+  sc->cnt[CNT_RZ] = 0;
+  sc->rho_new = rho_new;
+  if (sc->timeout) return;
+  if (!(rho_new > 0.0) || !finite(rho_new)) {
+    sc->status = ST_BREAKDOWN;
+    sc->done = 1;
+    return;
+  }
+  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
+  sc->rho = rho_new;
 }
 
 }  // namespace hbmc
