@@ -205,6 +205,34 @@ def test_initial_guess_and_restart(lib, orc):
     assert res2.status == H.OK and res2.iters == 0
 
 
+@pytest.mark.parametrize("precision", [H.PREC_F64, H.PREC_F32])
+def test_single_color_fused_preconditioner(lib, orc, precision):
+    """A system of one color: the last color is also the first, so the fused
+    forward-backward pass is the whole preconditioner and its own launch
+    reduces r.z.  Bulk-copy warp kernels forced (sweep_kernel 5) against the
+    block-per-level-1-block kernels (1), and FP64 against the oracle."""
+    A = W.poisson7(2)  # 8 unknowns, one 2x2x2 box, one color
+    b, _ = W.rhs_from_solution(A, 0)
+    outs = []
+    for sk in (5, 1):
+        ctx = H.hbmc_build(A, 8, 32, box=(2, 2, 2), sweep_kernel=sk, precision=precision)
+        assert ctx.info()["nc"] == 1
+        assert H.hbmc_ic0(ctx, 0.0)[0] == H.OK
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        res = H.hbmc_iccg(ctx, dev(b), x, tol=1e-10)
+        z = torch.empty(A.n, dtype=torch.float64, device="cuda")
+        H.hbmc_precond(ctx, dev(b), z)
+        outs.append((res.iters, host(x), host(z)))
+    assert outs[0][0] == outs[1][0]
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+    if precision == H.PREC_F64:
+        an = orc.analyse(A, 8, 32, box=(2, 2, 2))
+        lval, _, dinv, _ = orc.factor(an, 0.0)
+        ref = orc.pcg(an, lval, dinv, b, tol=1e-10)
+        assert outs[0][0] == ref.iters and _rel(outs[0][1], ref.x) <= 1e-12
+
+
 def test_edge_cases(lib, orc):
     A = W.poisson7(6)
     ctx, an, lval, ldiag, dinv = _setup(orc, A, 8, 32, (2, 2, 2))
