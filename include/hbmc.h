@@ -382,7 +382,8 @@ hbmc_status hbmc_sor_bar(hbmc_ctx *ctx, const double *b_dev, double *x_dev, doub
  * while a stream is captured into a CUDA graph (cudaMalloc is not allowed
  * then), programs whose device memory belongs entirely to another allocator,
  * or loops that must not allocate after start-up.  It computes what the
- * solver's SpMV computes (same bits in q), but keeps its reduction scratch
+ * solver's unsplit SpMV computes (same bits in q; with sell_split the
+ * solver's product is the row-split one instead), but keeps its reduction scratch
  * in a fixed array of static device memory inside the library: 16 bytes plus
  * 8192 doubles (64 KiB) per device, held by every GPU that loads the library
  * until the process exits.
