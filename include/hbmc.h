@@ -246,7 +246,9 @@ hbmc_status hbmc_get_factor(const hbmc_ctx *ctx, double *lower, double *diag);
  * hbmc_precond - z = (L L^T)^{-1} r in the original ordering: permute in,
  * forward substitution y = L^{-1} r (Eq. "for") over colors 1..n_c,
  * backward substitution z = L^{-T} y (Eq. "back") over colors n_c..1,
- * permute out.  r_dev, z_dev: device double[n] (may not alias).
+ * permute out.  Color n_c's forward and backward passes may run as one
+ * launch (the last color gathers nothing in the backward sweep); the bits
+ * are those of the two separate sweeps.  r_dev, z_dev: device double[n] (may not alias).
  * Asynchronous.  Errors: NOT_FACTORED, INVALID_ARG, CUDA.
  */
 hbmc_status hbmc_precond(hbmc_ctx *ctx, const double *r_dev, double *z_dev);
@@ -307,8 +309,11 @@ hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev);
  * times back to back on the context's own vectors: ms[0] forward
  * substitution (all colors), ms[1] backward substitution with the fused r.z
  * (all colors), ms[2] SpMV with the fused p.q, ms[3] x/r update with ||r||,
- * ms[4] p update.  Call it after a solve (the vectors then hold data of the
- * right scale); it leaves the context ready for the next solve.
+ * ms[4] p update.  The two sweeps are timed as separate launch sequences;
+ * inside a solve the last color's two passes may share one launch (so a
+ * solve's preconditioner can take less than ms[0] + ms[1]).  Call it after
+ * a solve (the vectors then hold data of the right scale); it leaves the
+ * context ready for the next solve.
  * Synchronizes the stream.
  */
 hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
