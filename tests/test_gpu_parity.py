@@ -263,9 +263,10 @@ def test_edge_cases(lib, orc):
     assert e.value.status == H.ERR_INVALID_ARG
 
 
-def test_empty_system_on_device(lib):
+@pytest.mark.parametrize("opts", [{}, {"sell_split": 16}, {"sweep_kernel": 7}, {"sweep_kernel": 5}])
+def test_empty_system_on_device(lib, opts):
     A = W.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
-    ctx = H.hbmc_build(A, 8, 32)
+    ctx = H.hbmc_build(A, 8, 32, **opts)
     assert H.hbmc_ic0(ctx)[0] == H.OK
     e = torch.zeros(0, dtype=torch.float64, device="cuda")
     r = H.hbmc_iccg(ctx, e, e)

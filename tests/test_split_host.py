@@ -48,3 +48,19 @@ def test_host_split_argument_checks(lib):
     assert ctx.info()["sell_entries_split"] == 0
     with pytest.raises(H.HbmcError):
         H.hbmc_get_split(ctx)
+
+
+def test_host_split_empty_and_single_row(lib, orc):
+    """An empty system gets an empty plan; a one-unknown system one slice
+    (the unknown and its dummies) with no cut."""
+    E = W.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    ctx = H.hbmc_build(E, 8, 32, host_only=True, sell_split=8)
+    inf = ctx.info()
+    assert (inf["n_pad"], inf["split_rows"], inf["split_pieces"], inf["sell_entries_split"]) == (0, 0, 0, 0)
+    assert H.hbmc_get_split(ctx).size == 0
+    one = W.CSR(1, np.array([0, 1], np.int64), np.array([0], np.int32), np.array([2.0]))
+    ctx = H.hbmc_build(one, 8, 32, host_only=True, sell_split=8)
+    an = orc.analyse(one, 8, 32)
+    plan = orc.split_plan(an.row_ptr, 32, 8, 2)
+    np.testing.assert_array_equal(H.hbmc_get_split(ctx), plan.head)
+    assert ctx.info()["split_rows"] == 0 and (plan.head == 1).all()
