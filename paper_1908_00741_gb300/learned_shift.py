@@ -4,8 +4,10 @@ Orchestration only: the sweeps are batched HBMC-ICCG solves, the features
 come from the library's feature kernel, and training is the library's
 forward/backward/Adam kernels (hbmc_mlp_train).  The network predicts
 log2(CG iterations) from [features, shift code]; the shift it recommends is
-the grid shift with the lowest prediction, and the plain positive-pivot rule
-(hbmc_ic0_auto without a network) stays the fallback and the judge.
+the grid shift with the lowest prediction.  The plain positive-pivot rule
+(hbmc_ic0_auto without a network) remains the fallback when the predicted
+shift's factorization fails, and the yardstick the learned choice is
+measured against.
 """
 from __future__ import annotations
 
