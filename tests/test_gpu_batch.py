@@ -140,3 +140,33 @@ def test_batch_autotune_and_cache(lib, tmp_path):
     assert ms[[4, 8, 16].index(best)] == ms.min()
     best2, ms2 = H.hbmc_batch_autotune(mats, b, (4, 8, 16), cache_path=cache)
     assert best2 == best and np.all(ms2 == -1)
+
+
+def test_batch_full_size_sampled(lib, orc):
+    """The 256-system batch at full size (n^3 with n in [16, 64], 7- or
+    27-point, 23.35 M unknowns) in the benchmark's launch configuration
+    (bs = 4, FP32 substitutions, FP64 CG): every system reaches the FP64
+    tolerance; then the same batch in FP64 gives, on the six smallest
+    systems, the oracle's iteration counts and x within 1e-12."""
+    items = W.batch_problems(256)
+    mats = [A for A, _, _ in items]
+    b = torch.tensor(_concat(items), device="cuda")
+    x = torch.zeros_like(b)
+    batch = H.hbmc_batch_build(mats, 4, precision=H.PREC_F32)
+    assert H.hbmc_batch_ic0(batch)[0] == H.OK
+    res = H.hbmc_batch_iccg(batch, b, x, tol=1e-8)
+    assert res.status == H.OK and np.all(res.statuses == H.OK)
+    assert np.all(res.true_relres < 1.1e-8)
+    del batch
+    batch = H.hbmc_batch_build(mats, 4, precision=H.PREC_F64)
+    assert H.hbmc_batch_ic0(batch)[0] == H.OK
+    x.zero_()
+    res = H.hbmc_batch_iccg(batch, b, x, tol=1e-8)
+    assert res.status == H.OK and np.all(res.statuses == H.OK)
+    xh = x.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([A.n for A in mats])])
+    for k in np.argsort([A.n for A in mats], kind="stable")[:6]:
+        A, bk, _ = items[k]
+        ref, _ = orc.iccg(A, bk, 4, 32, box=W.box_for_bs(4), tol=1e-8)
+        assert res.iters[k] == ref.iters, (k, res.iters[k], ref.iters)
+        assert _rel(xh[offs[k]:offs[k] + A.n], ref.x) <= 1e-12
