@@ -64,3 +64,37 @@ def test_host_split_empty_and_single_row(lib, orc):
     plan = orc.split_plan(an.row_ptr, 32, 8, 2)
     np.testing.assert_array_equal(H.hbmc_get_split(ctx), plan.head)
     assert ctx.info()["split_rows"] == 0 and (plan.head == 1).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_split_plan_random_matrices(lib, orc, seed):
+    """Random symmetric patterns with a few dense rows and columns (hubs), random
+    w, piece length and cost: the host plan equals the oracle's."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(50, 400))
+    M = sp.random(n, n, density=float(rng.uniform(0.005, 0.05)), random_state=int(rng.integers(1 << 30)))
+    hubs = rng.choice(n, size=max(1, n // 50), replace=False)
+    H_ = sp.lil_matrix((n, n))
+    for h in hubs:
+        cols = rng.choice(n, size=min(n, int(rng.integers(n // 4, n))), replace=False)
+        H_[h, cols] = 1.0
+    S = (M + M.T + H_ + H_.T).tocsr()
+    S.setdiag(0.0)
+    S.eliminate_zeros()
+    S = S + sp.identity(n) * (abs(S).sum(axis=1).max() + 1.0)
+    S = S.tocsr()
+    S.sort_indices()
+    A = W.CSR(n, S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data.astype(np.float64))
+    bs = int(rng.choice([1, 2, 4, 8]))
+    w = int(rng.choice([4, 8, 16, 32]))
+    P = int(rng.choice([2, 8, 32]))
+    cost = int(rng.integers(0, 4))
+    ctx = H.hbmc_build(A, bs, w, host_only=True, sell_split=P, sell_split_cost=cost)
+    an = orc.analyse(A, bs, w)
+    plan = orc.split_plan(an.row_ptr, w, P, cost if cost > 0 else 2)
+    np.testing.assert_array_equal(H.hbmc_get_split(ctx), plan.head)
+    inf = ctx.info()
+    assert (inf["split_rows"], inf["split_pieces"], inf["sell_entries_split"]) == \
+        (plan.nsplit, plan.npieces, plan.processed)
+

@@ -195,3 +195,32 @@ def test_structural_sell_padding_like_audikw(orc):
         ln = np.diff(np.asarray(an.row_ptr))
         out[w] = (ln.reshape(-1, w).max(1) * w).sum() / ln.sum() - 1.0
     assert 0.15 < out[4] < 0.40 and 0.25 < out[8] < 0.55 and out[8] > out[4]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_plan_random_length_mixes(orc, seed):
+    """Many random row-length mixes (uniform, heavy-tailed, a few very long
+    rows, empty-ish slices of length-1 rows) against the explicitly cut plan."""
+    rng = np.random.default_rng(100 + seed)
+    w = int(rng.choice([1, 2, 4, 8, 16, 32]))
+    ns = int(rng.integers(1, 6))
+    kind = seed % 4
+    n = ns * w
+    if kind == 0:
+        lengths = rng.integers(1, 20, size=n)
+    elif kind == 1:
+        lengths = np.minimum(1 + rng.pareto(1.5, size=n) * 5, 300).astype(np.int64)
+    elif kind == 2:
+        lengths = np.full(n, 5)
+        lengths[rng.choice(n, size=max(1, n // 16), replace=False)] = rng.integers(50, 200)
+    else:
+        lengths = np.ones(n, dtype=np.int64)
+        lengths[::3] = rng.integers(1, 40, size=len(lengths[::3]))
+    P = int(rng.choice([1, 3, 8, 64]))
+    cost = int(rng.integers(0, 5))
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(lengths)
+    plan = orc.split_plan(rp, w, piece=P, cost=cost)
+    head, processed, npieces = _explicit_plan(list(lengths), w, P, cost)
+    np.testing.assert_array_equal(plan.head, head)
+    assert (plan.processed, plan.npieces) == (processed, npieces)
