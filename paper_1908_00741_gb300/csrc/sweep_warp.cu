@@ -141,31 +141,7 @@ __global__ void __launch_bounds__(32 * kMaxWpb)
     }
   }
   if (!dot_mode) return;
-  const double v = block_sum_rt(rz);
-  if (threadIdx.x == 0) part[part_off + blockIdx.x] = v;
-  if (!last_launch) return;
-  __shared__ unsigned s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(&sc->cnt[CNT_RZ], 1u);
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < part_total; k += blockDim.x) acc += __ldcg(part + k);
-  const double rho_new = block_sum_rt(acc);
-  if (threadIdx.x != 0) return;
-  sc->cnt[CNT_RZ] = 0;
-  sc->rho_new = rho_new;
-  if (!(rho_new > 0.0) || !finite(rho_new)) {
-    sc->status = ST_BREAKDOWN;
-    sc->done = 1;
-    return;
-  }
-  if (dot_mode == 2) sc->beta = rho_new / sc->rho;
-  sc->rho = rho_new;
+  rz_partial(rz, sc, dot_mode, part, part_off + blockIdx.x, last_launch, part_total, gridDim.x);
 }
 
 // q = A p over every unit (all colors in one launch), with p.q and alpha.
