@@ -84,10 +84,11 @@ typedef struct hbmc_options {
   int32_t check_every; /* HBMC_LOOP_HOST: iterations between flag polls (default 16) */
   int32_t sweep_tpb;   /* level-1 blocks per CUDA block in the substitution kernels;
                           0 = automatic, else a power of two with sweep_tpb * w <= 256 */
-  int32_t sweep_kernel; /* substitution kernels: 0 = automatic (one warp per level-1 block
-                           when w = 32 and its runs fit in shared memory -- right-hand side,
-                           dinv and same-block runs staged by bulk copy when bs is 4 or 8 --
-                           else 1);
+  int32_t sweep_kernel; /* substitution kernels: 0 = automatic (8 when the matrix has 8 or
+                           more colors and two of its CUDA blocks fit on an SM; else one warp
+                           per level-1 block when w = 32 and its runs fit in shared memory --
+                           right-hand side, dinv and same-block runs staged by bulk copy when
+                           bs is 4 or 8 -- else 1);
                            1 = one CUDA block per level-1 block(s);
                            2 = TMA-fed persistent warp-specialized kernels (w = 32);
                            3 = one warp per level-1 block reading its runs with plain loads,
@@ -105,7 +106,13 @@ typedef struct hbmc_options {
                                bs CUDA blocks, one per step, the last of which to finish
                                runs the chains (automatic under 0 for colors with fewer
                                than two level-1 blocks per SM whose other-color runs
-                               average 12288 or more entries).
+                               average 12288 or more entries);
+                           8 = dependency-driven: each sweep is one launch over every
+                               color, one CUDA block per level-1 block; a level-1 block
+                               waits only for the level-1 blocks of other colors whose
+                               rows it reads (Section 4.3.3's n_c - 1 synchronizations
+                               per sweep become per-block flags), needs w = 32 and its
+                               runs in shared memory, else as 0.
                            SpMV (w = 32) is fed by bulk copies when a chunk of its slices fits
                            in shared memory, else one thread per row; with 3 it runs one warp
                            per level-1 block. */
@@ -319,6 +326,19 @@ hbmc_status hbmc_spmv_bar(hbmc_ctx *ctx, const double *p_dev, double *q_dev);
 hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
 
 /*
+ * hbmc_debug_stall - test hook for the bounded waits of the
+ * dependency-driven sweeps (sweep_kernel 8); the paper has no counterpart.
+ * unit >= 0: level-1 block `unit` (0-based, HBMC order) computes its rows
+ * but never publishes its completion flag, so every level-1 block that
+ * gathers from it waits until wait_s seconds have passed, gives up, and the
+ * solve returns HBMC_ERR_TIMEOUT with the context still usable.  unit = -1
+ * restores normal operation; wait_s <= 0 restores the default bound (4 s).
+ * Takes effect at the next launch; a solve graph captured earlier keeps the
+ * values it was captured with, so the hook discards the context's graphs.
+ */
+hbmc_status hbmc_debug_stall(hbmc_ctx *ctx, int64_t unit, double wait_s);
+
+/*
  * hbmc_ilu0 - ILU(0) of Abar for a context built with opt.nonsymmetric = 1
  * (Section 2: ILU(0) preconditioning; the HBMC ordering makes its
  * substitutions parallel exactly as for IC(0), with U in place of L^T).
@@ -394,8 +414,9 @@ hbmc_status hbmc_sor_bar(hbmc_ctx *ctx, const double *b_dev, double *x_dev, doub
  * until the process exits.
  *
  * p_dev, q_dev: device double[n_pad] in HBMC order (p may not alias q);
- * pq_dev: device double receiving p.q.  Asynchronous on the context's
- * stream.  Needs a context built with w = 32 and at most 32768 level-1
+ * pq_dev: device double receiving p.q.  For an empty system (n = 0) only
+ * pq_dev is used (set to 0; p_dev and q_dev may be NULL).  Asynchronous on
+ * the context's stream.  Needs a context built with w = 32 and at most 32768 level-1
  * blocks (n_pad <= 32768 * bs * 32); larger contexts get
  * HBMC_ERR_INVALID_ARG with the limit in hbmc_last_error.  Calls no
  * cudaMalloc or cudaFree.  The first call on a device looks up the static

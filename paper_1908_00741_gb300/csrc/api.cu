@@ -228,6 +228,26 @@ hbmc_status upload(hbmc_ctx *ctx) {
   CK(hbmc::setup_spmv_tma());
   hbmc::plan_wide_kernels(h, d);
   CK(hbmc::setup_wide_kernels());
+  if (have_x && h.w == 32) {
+    hbmc::DagTables t;
+    if (hbmc::dag_host_tables(h, t)) {
+      TRY(dupload(ctx, d.dag_unit_color, t.ucolor));
+      TRY(dupload(ctx, d.dag_color_units, t.color_units));
+      TRY(dalloc(ctx, d.dag_color_done, 2 * (size_t)h.nc));
+      TRY(dalloc(ctx, d.dag_exit, 2));
+      TRY(dupload(ctx, d.dep_ptr_f, t.ptr_f));
+      TRY(dupload(ctx, d.dep_f, t.dep_f));
+      TRY(dupload(ctx, d.dep_ptr_b, t.ptr_b));
+      TRY(dupload(ctx, d.dep_b, t.dep_b));
+      TRY(dupload(ctx, d.dag_order_b, t.order_b));
+      TRY(dalloc(ctx, d.dag_flag_f, (size_t)h.ntiles));
+      TRY(dalloc(ctx, d.dag_flag_b, (size_t)h.ntiles));
+      TRY(dalloc(ctx, d.dag_abort, 2));
+      TRY(dalloc(ctx, d.dag_ticket, 2));
+      hbmc::plan_dag_kernels(h, d);
+      CK(hbmc::setup_dag_kernels());
+    }
+  }
   hbmc::plan_sor(h, d);
   CK(hbmc::setup_sor());
   CK(hbmc::setup_persistent());
@@ -384,8 +404,9 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
     // and two preconditioner applications (4 n_c sweeps).
     // Row-split SpMV: one more launch for the pieces; the fused last color
     // of the preconditioner: one launch fewer.
+    // Dependency-driven sweeps: one launch per sweep.
     const int64_t fb = !bicg && hbmc::fb_tw_usable(d, prec) ? 1 : 0;
-    const int64_t nc = d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc + (d.split && d.n_virt > 0 ? 1 : 0) - fb;
+    const int64_t nc = hbmc::dag_selected(d, prec) ? 1 : d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc + (d.split && d.n_virt > 0 ? 1 : 0) - fb;
     int64_t passes = r.iters > 0 ? r.iters : 1;
     if (ctx->opt.loop_mode == HBMC_LOOP_HOST) {
       const int64_t every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
@@ -453,8 +474,8 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sell_split and sell_split_cost must be >= 0");
   if (o.sell_split > 0 && w > 32)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "row splitting needs w <= 32");
-  if (o.sweep_kernel < 0 || o.sweep_kernel > 7)
-    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..7");
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 8)
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..8");
   if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_tpb must be 0 or a power of two with sweep_tpb * w <= 256");
   hbmc_ctx *ctx = nullptr;
@@ -506,6 +527,28 @@ void hbmc_destroy(hbmc_ctx *ctx) {
     if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
   }
   delete ctx;
+}
+
+hbmc_status hbmc_debug_stall(hbmc_ctx *ctx, int64_t unit, double wait_s) {
+  TRY(need_device(ctx));
+  if (unit >= ctx->h.ntiles) return set_err(ctx, HBMC_ERR_INVALID_ARG, "unit beyond the last level-1 block");
+  if (!(wait_s <= 1e6)) return set_err(ctx, HBMC_ERR_INVALID_ARG, "wait_s must be a number of seconds <= 1e6");
+  DeviceGuard guard(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->d.dag_stall = unit < 0 ? -1 : unit;
+  ctx->d.dag_wait_ns = wait_s > 0.0 ? (uint64_t)(wait_s * 1e9) : 4000000000ull;
+  // the kernels' arguments are fixed inside a captured graph
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->exec[k]) cudaGraphExecDestroy(ctx->exec[k]);
+    if (ctx->graph[k]) cudaGraphDestroy(ctx->graph[k]);
+    if (ctx->bexec[k]) cudaGraphExecDestroy(ctx->bexec[k]);
+    if (ctx->bgraph[k]) cudaGraphDestroy(ctx->bgraph[k]);
+    ctx->exec[k] = nullptr;
+    ctx->graph[k] = nullptr;
+    ctx->bexec[k] = nullptr;
+    ctx->bgraph[k] = nullptr;
+  }
+  return HBMC_OK;
 }
 
 hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info) {

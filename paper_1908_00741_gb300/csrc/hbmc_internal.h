@@ -182,6 +182,14 @@ struct WidePlan {
   bool ok = false;
 };
 
+// Shared memory of the dependency-driven sweeps (sweep_dag.cu), byte
+// offsets; ok = false when a level-1 block's runs do not fit.
+struct DagPlan {
+  uint32_t off_xr = 0, off_ts = 0, off_tin = 0, off_ds = 0, off_rr = 0, off_oc = 0, off_vv = 0, off_iv = 0,
+           off_im = 0, smem_bytes = 0;
+  bool ok = false;
+};
+
 // Shared memory of the SOR sweep kernel (sor.cu), byte offsets.
 struct SorPlan {
   uint32_t off_cb = 0, off_bb = 0, off_dd = 0, off_sv = 0, off_ix = 0, smem_bytes = 0;
@@ -236,6 +244,20 @@ struct DeviceLayout {
   WidePlan ws_f64_f, ws_f64_b, ws_f32_f, ws_f32_b;  // split over several CUDA blocks per level-1 block
   std::vector<uint8_t> wide_f, wide_b;  // per color: 1 = loader-thread sweep, 2 = its split form
   unsigned *ucnt = nullptr;  // per level-1 block arrival counters of the split form (zero between launches)
+  // dependency-driven sweeps: per level-1 block what it waits for
+  // (forward, backward), the backward sweep's order, level-1 block -> color
+  // and color -> level-1 blocks, the completion flags and counters, the
+  // ticket counters and abort words ([0] forward, [1] backward), and the test hook (a level-1 block that never publishes,
+  // and the bound of every wait)
+  int64_t *dep_ptr_f = nullptr, *dep_ptr_b = nullptr, *dag_color_units = nullptr;
+  int32_t *dep_f = nullptr, *dep_b = nullptr, *dag_order_b = nullptr, *dag_unit_color = nullptr;
+  unsigned *dag_flag_f = nullptr, *dag_flag_b = nullptr, *dag_abort = nullptr;
+  unsigned *dag_color_done = nullptr;  // per color, forward then backward (cleared by each launch's last block)
+  unsigned *dag_exit = nullptr;        // finished CUDA blocks of the running launch, forward and backward
+  unsigned long long *dag_ticket = nullptr;
+  DagPlan dg_f64_f, dg_f64_b, dg_f32_f, dg_f32_b;
+  int64_t dag_stall = -1;
+  uint64_t dag_wait_ns = 4000000000ull;
   int32_t lw = 0;        // log2(w)
   int64_t max_in_f = 0, max_in_b = 0;
   int32_t in_smem_f = 0, in_smem_b = 0;

@@ -692,6 +692,7 @@ void enqueue_spmv_plain(const DeviceLayout &d, const double *p, double *q, bool 
 // with long other-color runs or few level-1 blocks, else the
 // bulk-copy-staged warp kernel; both give the same bits.
 void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
+  if (dag_selected(d, prec)) return enqueue_fwd_dag(d, prec, r, check_done, s);
   const bool wide = wide_usable(d, true, prec), tw = tw_usable(d, true, prec);
   if ((wide && wide_all(d)) || tw) {
     for (int c = 0; c < d.nc; ++c) {
@@ -717,6 +718,7 @@ void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_do
 // Backward sweep over all colors (n_c..1): z from y / y32; dot_mode 0: no
 // dot, 1: initial rho = r.z, 2: rho and beta.
 void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done, cudaStream_t s) {
+  if (dag_selected(d, prec)) return enqueue_bwd_dag(d, prec, r, dot_mode, check_done, s);
   const bool wide = wide_usable(d, false, prec), tw = tw_usable(d, false, prec);
   if ((wide && wide_all(d)) || tw) {
     auto use_wide = [&](int c) { return wide && wide_preferred(d, false, c); };

@@ -51,6 +51,22 @@ void launch_fwd_wide_color(const DeviceLayout &d, int prec, int c, const double 
 void launch_bwd_wide_color(const DeviceLayout &d, int prec, int c, const double *r, int dot_mode, bool check_done,
                            int64_t part_off, bool last, int64_t part_total, cudaStream_t s);
 
+// Dependency-driven sweeps: every color in one launch (sweep_dag.cu).
+// Host tables: per level-1 block what it waits for (forward / backward), the
+// backward sweep's order, level-1 block -> color, color -> level-1 blocks.
+struct DagTables {
+  std::vector<int64_t> ptr_f, ptr_b, color_units;
+  std::vector<int32_t> dep_f, dep_b, order_b, ucolor;
+};
+bool dag_host_tables(const HostLayout &h, DagTables &t);
+void plan_dag_kernels(const HostLayout &h, DeviceLayout &d);
+cudaError_t setup_dag_kernels();
+bool dag_usable(const DeviceLayout &d, bool fwd, int prec);
+bool dag_selected(const DeviceLayout &d, int prec);
+void enqueue_fwd_dag(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
+void enqueue_bwd_dag(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
+                     cudaStream_t s);
+
 // Bulk-copy-fed SpMV, w = 32 (spmv_tma.cu)
 void plan_spmv_tma(const HostLayout &h, DeviceLayout &d);
 cudaError_t setup_spmv_tma();

@@ -163,7 +163,24 @@ extern "C" hbmc_status hbmc_spmv_dot_static(hbmc_ctx *ctx, const double *p_dev, 
   bool factored = false;
   std::string *err = nullptr;
   if (!hbmc::ctx_view(ctx, &d, &stream, &dev, &factored, &err)) return HBMC_ERR_NO_DEVICE;
-  if (d->n == 0) return HBMC_OK;
+  if (d->n == 0) {
+    // nothing to multiply; p.q of empty vectors is 0, written so that the
+    // caller never reads a stale value after a successful call
+    if (!pq_dev) {
+      *err = "hbmc_spmv_dot_static: null pointer";
+      return HBMC_ERR_INVALID_ARG;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+    const cudaError_t e = cudaMemsetAsync(pq_dev, 0, sizeof(double), stream);
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+      *err = std::string("hbmc_spmv_dot_static: ") + cudaGetErrorString(e);
+      return HBMC_ERR_CUDA;
+    }
+    return HBMC_OK;
+  }
   if (!p_dev || !q_dev || !pq_dev) {
     *err = "hbmc_spmv_dot_static: null pointer";
     return HBMC_ERR_INVALID_ARG;

@@ -404,6 +404,7 @@ void plan_tw_kernels(const HostLayout &h, DeviceLayout &d) {
 // for the last color, one dinv for both (IC(0)), and its plan fits.
 bool fb_tw_usable(const DeviceLayout &d, int prec) {
   if (d.nc < 1 || !tw_usable(d, true, prec) || !tw_usable(d, false, prec)) return false;
+  if (dag_selected(d, prec)) return false;
   if (d.dinvb != d.dinv || d.dinvb32 != d.dinv32) return false;
   const int c = d.nc - 1;
   if (wide_usable(d, true, prec) && wide_preferred(d, true, c)) return false;

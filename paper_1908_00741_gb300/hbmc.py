@@ -46,7 +46,7 @@ EXPORTED = [
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
-    "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar", "hbmc_ilu0", "hbmc_get_factor_u", "hbmc_bicgstab",
+    "hbmc_debug_stall", "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar", "hbmc_ilu0", "hbmc_get_factor_u", "hbmc_bicgstab",
     "hbmc_batch_build", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
     "hbmc_batch_set_stream", "hbmc_batch_set_precision", "hbmc_batch_ic0", "hbmc_batch_iccg",
     "hbmc_batch_autotune", "hbmc_batch_features",
@@ -124,6 +124,7 @@ def load():
             "hbmc_bwd_bar": (I32, [P, P, P]),
             "hbmc_spmv_bar": (I32, [P, P, P]),
             "hbmc_profile_kernels": (I32, [P, I32, P]),
+            "hbmc_debug_stall": (I32, [P, I64, D]),
             "hbmc_spmv_dot_static": (I32, [P, P, P, P]),
             "hbmc_sor": (I32, [P, P, P, D, I32, I32, P]),
             "hbmc_sor_bar": (I32, [P, P, P, D, I32, I32]),
@@ -431,6 +432,13 @@ def hbmc_profile_kernels(ctx: Context, reps: int = 20) -> dict:
     out = np.zeros(5)
     ctx.check(ctx._lib.hbmc_profile_kernels(ctx.handle, int(reps), _np_ptr(out)))
     return dict(zip(PROFILE_PHASES, out.tolist()))
+
+
+def hbmc_debug_stall(ctx: Context, unit: int = -1, wait_s: float = 0.0) -> None:
+    """Test hook of the dependency-driven sweeps: level-1 block `unit` never
+    publishes its completion, and every wait gives up after wait_s seconds
+    (unit = -1, wait_s = 0: normal operation)."""
+    ctx.check(ctx._lib.hbmc_debug_stall(ctx.handle, int(unit), float(wait_s)))
 
 
 def hbmc_spmv_dot_static(ctx: Context, p, q, pq) -> None:

@@ -387,10 +387,11 @@ def test_sweep_kernel_variants_agree(lib, orc, name, mk, bs, w, box, precision):
     per level-1 block with plain loads, 4 loader-thread blocks staged by bulk
     copy, 5 warp per level-1 block staged by bulk copy (bs 4 and 8), 6
     loader-thread blocks with plain loads, 7 loader-thread sweeps split over
-    bs CUDA blocks per level-1 block."""
+    bs CUDA blocks per level-1 block, 8 dependency-driven (every color in one
+    launch)."""
     A = mk()
     outs = []
-    for sk in (0, 1, 2, 3, 4, 5, 6, 7):
+    for sk in (0, 1, 2, 3, 4, 5, 6, 7, 8):
         ctx = H.hbmc_build(A, bs, w, box=box, sweep_kernel=sk, precision=precision)
         assert H.hbmc_ic0(ctx, 0.1)[0] == H.OK
         n_pad = ctx.info()["n_pad"]
@@ -445,40 +446,47 @@ def test_mc_bmc_hbmc_orderings(lib, orc):
 @pytest.mark.parametrize("which", ["hetero27_96", "veclap_100"])
 def test_full_size_algebraic(lib, orc, which):
     """The random-order configurations at full size, in the launch
-    configuration of the benchmark (bs = 8, w = 32, algebraic blocking; the
-    loader-thread sweeps for their many small colors): IC(0), both
-    substitutions and SpMV bit-equal to the oracle, the FP64 solve with the
-    oracle's iteration count and x within 1e-12, and the FP32-substitution
-    solve to the FP64 tolerance."""
+    configuration of the benchmark (bs = 8, w = 32, algebraic blocking), with
+    the automatic choice (the dependency-driven sweeps for these many-color
+    matrices) and with the per-color loader-thread kernels (sweep_kernel 4):
+    IC(0), both substitutions and SpMV bit-equal to the
+    oracle, the FP64 solve with the oracle's iteration count and x within
+    1e-12, and the FP32-substitution solve to the FP64 tolerance."""
     P = W.heterogeneous27_problem(96) if which == "hetero27_96" else W.vector_laplacian_problem(100)
-    ctx, an, lval, ldiag, dinv = _setup(orc, P.A, 8, 32, None)
-    assert ctx.info()["nc"] > 10
-    glo, gdiag = H.hbmc_get_factor(ctx)
-    rows = np.repeat(np.arange(an.n_pad), np.diff(an.row_ptr))
-    low = an.col < rows
-    np.testing.assert_array_equal(glo[low], lval[low])
-    np.testing.assert_array_equal(gdiag, ldiag)
+    an = orc.analyse(P.A, 8, 32)
+    lval, ldiag, dinv, obad = orc.factor(an, 0.0)
+    assert obad == -1
     r = np.random.default_rng(17).standard_normal(an.n_pad)
     y_ref = orc.fwd(an.row_ptr, an.col, lval, dinv, r)
     z_ref = orc.bwd(an.row_ptr, an.col, lval, dinv, y_ref)
     q_ref = orc.spmv(an.row_ptr, an.col, an.val, r)
-    y, z, q = (torch.empty(an.n_pad, dtype=torch.float64, device="cuda") for _ in range(3))
-    H.hbmc_fwd_bar(ctx, dev(r), y)
-    H.hbmc_bwd_bar(ctx, dev(y_ref), z)
-    H.hbmc_spmv_bar(ctx, dev(r), q)
-    np.testing.assert_array_equal(host(y), y_ref)
-    np.testing.assert_array_equal(host(z), z_ref)
-    np.testing.assert_array_equal(host(q), q_ref)
-    x = torch.zeros(P.A.n, dtype=torch.float64, device="cuda")
-    res = H.hbmc_iccg(ctx, dev(P.b), x, tol=1e-8)
     ref = orc.pcg(an, lval, dinv, P.b, tol=1e-8)
-    assert res.status == H.OK and res.iters == ref.iters
-    assert _rel(host(x), ref.x) <= 1e-12
-    H.hbmc_set_precision(ctx, H.PREC_F32)
-    x.zero_()
-    res32 = H.hbmc_iccg(ctx, dev(P.b), x, tol=1e-8)
-    assert res32.status == H.OK and res32.true_relres < 1.1e-8
-    assert abs(res32.iters - ref.iters) <= max(2, ref.iters // 20)
+    rows = np.repeat(np.arange(an.n_pad), np.diff(an.row_ptr))
+    low = an.col < rows
+    for sk in (0, 4):
+        ctx = H.hbmc_build(P.A, 8, 32, sweep_kernel=sk)
+        assert H.hbmc_ic0(ctx, 0.0) == (H.OK, -1)
+        assert ctx.info()["nc"] > 10
+        glo, gdiag = H.hbmc_get_factor(ctx)
+        np.testing.assert_array_equal(glo[low], lval[low])
+        np.testing.assert_array_equal(gdiag, ldiag)
+        y, z, q = (torch.empty(an.n_pad, dtype=torch.float64, device="cuda") for _ in range(3))
+        H.hbmc_fwd_bar(ctx, dev(r), y)
+        H.hbmc_bwd_bar(ctx, dev(y_ref), z)
+        H.hbmc_spmv_bar(ctx, dev(r), q)
+        np.testing.assert_array_equal(host(y), y_ref)
+        np.testing.assert_array_equal(host(z), z_ref)
+        np.testing.assert_array_equal(host(q), q_ref)
+        x = torch.zeros(P.A.n, dtype=torch.float64, device="cuda")
+        res = H.hbmc_iccg(ctx, dev(P.b), x, tol=1e-8)
+        assert res.status == H.OK and res.iters == ref.iters, (sk, res.iters, ref.iters)
+        assert _rel(host(x), ref.x) <= 1e-12
+        H.hbmc_set_precision(ctx, H.PREC_F32)
+        x.zero_()
+        res32 = H.hbmc_iccg(ctx, dev(P.b), x, tol=1e-8)
+        assert res32.status == H.OK and res32.true_relres < 1.1e-8
+        assert abs(res32.iters - ref.iters) <= max(2, ref.iters // 20)
+        del ctx
 
 
 @pytest.mark.parametrize("precision", [H.PREC_F64, H.PREC_F32])

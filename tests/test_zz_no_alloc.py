@@ -52,6 +52,17 @@ def test_static_scratch_spmv_matches_spmv_bar(lib, name, mk, bs, box):
         assert abs(pq.item() - ref) <= 1e-12 * abs(ref)
 
 
+def test_static_scratch_empty_system_sets_pq_to_zero(lib):
+    A = W.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    ctx = H.hbmc_build(A, 8, 32)
+    p = torch.zeros(0, dtype=torch.float64, device="cuda")
+    q = torch.zeros_like(p)
+    pq = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    H.hbmc_spmv_dot_static(ctx, p, q, pq)
+    torch.cuda.synchronize()
+    assert pq.item() == 0.0
+
+
 def test_static_scratch_refuses_oversized_systems(lib):
     A = W.poisson7(104)  # bs = 1: 1,124,864 rows = 35,152 level-1 blocks > 32,768
     ctx = H.hbmc_build(A, 1, 32)
