@@ -7,9 +7,19 @@ x* ~ U(-1, 1), x0 = 0, tolerance 1e-8.  A step is one complete hbmc_iccg
 call: permute b in, the CG loop with both substitutions, permute x out and
 the true residual; the IC(0) factorization is timed separately.
 
+The line also carries, under "configs", the other configurations in the
+launch configuration the library picks for them (skip with --no-configs):
+the heterogeneous 27-point 96^3 and 3-DOF vector-Laplacian 100^3 systems in
+a random order with FP32 substitutions (time, iterations, residual, per-sweep
+bandwidth), the 256-system batch (autotuned, aggregate bandwidth, per-system
+times) and the learned IC shift (trained on the GPU from shift sweeps,
+held-out gain over the plain rule, and its use on those configurations and
+on an IEEJ-sized curl-curl system).
+
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
-the host cores instead (each step a bounded sample of the same solve, scaled
-to the full iteration count).
+the host cores instead (each step a bounded sample of the same solve: the
+start of the solve plus a few PCG iterations, extrapolated to the full
+iteration count).
 """
 from __future__ import annotations
 
@@ -154,6 +164,38 @@ def measured_traffic():
 FP64_NOMINAL_TFLOPS = 1.25
 
 
+# The roofline the scope statement names: bytes over 8 TB/s (nominal HBM3e).
+# Every fraction is also given against the measured copy bandwidth.
+HBM_NOMINAL_GBS = 8000.0
+
+
+def host_info():
+    """This host's core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            model = "unknown"
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+def fracs(gbs, peak):
+    return {"frac": round(gbs / peak, 4), "frac_nominal": round(gbs / HBM_NOMINAL_GBS, 4)}
+
+
 def subst_bytes(n, nnz_lower, s):
     """Algorithmic bytes of one forward / backward substitution (compulsory
     traffic: each nonzero of L once with its int32 column, dinv, the input
@@ -290,8 +332,8 @@ def run_gpu(args):
                 "fp64": {"fma_per_launch": sp_fma, "achieved_tflops": round(sp_tflops, 4),
                          "peak_tflops": FP64_NOMINAL_TFLOPS, "frac": round(sp_tflops / FP64_NOMINAL_TFLOPS, 4),
                          "peak_source": "nominal"}}
-    subst = {k: {"GB/s": round(v, 1), "frac": round(v / peak, 4), "ms": round(kernel_ms[k], 4)}
-             for k, v in gbs.items()}
+    roofline.update({"frac_nominal": round(gbs["spmv"] / HBM_NOMINAL_GBS, 4), "peak_nominal": HBM_NOMINAL_GBS})
+    subst = {k: {"GB/s": round(v, 1), **fracs(v, peak), "ms": round(kernel_ms[k], 4)} for k, v in gbs.items()}
 
     variants = {}
     if not args.no_variants:
@@ -341,6 +383,17 @@ def run_gpu(args):
                                             "true_relres": rv.true_relres}
                 cv.close()
 
+    configs = {}
+    if not args.no_configs:
+        # the other configurations, each in the launch configuration the
+        # library picks for it (FP32 substitutions in FP64 CG, as specified)
+        configs["hetero27_96_f32"] = config_solve(W.heterogeneous27_problem(args.hetero_m), H.PREC_F32, local,
+                                                  stream, peak, "heterogeneous 27-point 96^3, random order")
+        configs["veclap_100_f32"] = config_solve(W.vector_laplacian_problem(args.veclap_m), H.PREC_F32, local,
+                                                 stream, peak, "3-DOF vector Laplacian 100^3 nodes, random order")
+        configs["batch256_f32"] = batch_report(args, local, peak)
+        configs["learned_shift"] = learned_report(args, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(P, iters, args.cpu_sample_iters)
@@ -364,7 +417,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 2 * A.n * 8,
                 "d2h_bytes_per_step": A.n * 8},
         "gpu_launches": int(total_launches), "launches_per_step": int(launches),
-        "roofline": roofline, "subst_roofline": subst, "variants": variants,
+        "roofline": roofline, "subst_roofline": subst, "variants": variants, "configs": configs,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -382,28 +435,74 @@ def cpu_baseline(P, gpu_iters, sample_iters):
     lval, _, dinv, bad = oracle.factor(an, 0.0)
     setup_s = time.perf_counter() - t
     t = time.perf_counter()
+    oracle.pcg(an, lval, dinv, P.b, tol=TOL, maxit=0)
+    start_s = time.perf_counter() - t
+    t = time.perf_counter()
     s = oracle.pcg(an, lval, dinv, P.b, tol=TOL, maxit=sample_iters)
     dt = time.perf_counter() - t
-    per_iter = dt / max(s.iters, 1)
-    return {"value": round(per_iter * gpu_iters * 1e3, 3), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"{s.iters} PCG iterations of the 128^3 solve ({dt:.2f} s, + {setup_s:.2f} s setup "
-                      f"not counted), scaled to {gpu_iters} iterations"}
+    per_iter = max(dt - start_s, 0.0) / max(s.iters, 1)
+    return {"value": round((start_s + per_iter * gpu_iters) * 1e3, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"the start and {s.iters} PCG iterations of the 128^3 solve ({dt:.2f} s, + {setup_s:.2f} s "
+                      f"setup not counted); value = start + per-iteration time x {gpu_iters} iterations",
+            "scaled_from_iters": int(s.iters), "sample_s": round(dt, 3), "host": host_info()}
+
+
+def config_solve(P, prec, local, stream, peak, name, reps=5):
+    """One configuration: solve time (CUDA events, inputs resident), CG
+    iterations, true residual, and the per-sweep device times with their
+    algorithmic bandwidth against the measured and the nominal HBM peak."""
+    import torch
+    from paper_1908_00741_gb300 import hbmc as H
+    t = time.perf_counter()
+    ctx = H.hbmc_build(P.A, P.bs, 32, box=P.box, precision=prec, device=local)
+    build_s = time.perf_counter() - t
+    H.hbmc_set_stream(ctx, stream)
+    st, bad = H.hbmc_ic0(ctx)
+    assert st == H.OK, bad
+    b = torch.tensor(P.b, device="cuda")
+    x = torch.zeros_like(b)
+    for _ in range(2):
+        x.zero_()
+        res = H.hbmc_iccg(ctx, b, x, tol=TOL)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        x.zero_()
+        res = H.hbmc_iccg(ctx, b, x, tol=TOL)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    prof = H.hbmc_profile_kernels(ctx, 20)
+    inf = ctx.info()
+    s = 4 if prec == H.PREC_F32 else 8
+    fb, bb = subst_bytes(P.A.n, inf["nnz_lower"], s)
+    fwd_gbs = fb / (prof["fwd"] * 1e-3) / 1e9
+    bwd_gbs = bb / (prof["bwd"] * 1e-3) / 1e9
+    sp_gbs = spmv_bytes(P.A.n, P.A.nnz) / (prof["spmv"] * 1e-3) / 1e9
+    out = {"workload": name, "n": P.A.n, "nnz": P.A.nnz, "bs": P.bs, "w": 32, "colors": inf["nc"],
+           "precision": "f32" if s == 4 else "f64", "ms": round(ms, 3), "iters": res.iters,
+           "status": res.status, "true_relres": res.true_relres, "ms_per_iter": round(ms / max(res.iters, 1), 4),
+           "build_s": round(build_s, 2), "launches_per_solve": inf["last_launches"],
+           "subst_roofline": {
+               "fwd": {"ms": round(prof["fwd"], 4), "GB/s": round(fwd_gbs, 1), **fracs(fwd_gbs, peak)},
+               "bwd": {"ms": round(prof["bwd"], 4), "GB/s": round(bwd_gbs, 1), **fracs(bwd_gbs, peak)},
+               "spmv": {"ms": round(prof["spmv"], 4), "GB/s": round(sp_gbs, 1), **fracs(sp_gbs, peak)}}}
+    ctx.close()
+    return out
 
 
 # --------------------------------------------------------------------------
 # batched workload: 256 uneven systems
 # --------------------------------------------------------------------------
 
-def run_batch(args):
-    """256 independent SPD systems (7- or 27-point, n^3 with n ~ U{16..64},
-    lognormal sigma ~ U[0, 2]) solved together; block size chosen by the
-    library's autotuner on a 32-system subset; FP32 substitutions, FP64 CG."""
+def batch_report(args, local, peak, steps=3, warmup=2):
+    """The 256-system batch (FP32 substitutions, FP64 CG): autotuned on a
+    32-system subset, then solved together.  Aggregate algorithmic bandwidth:
+    every system's per-iteration bytes (SpMV, both FP32 substitutions, nine
+    vector passes) times its iterations, over the batch's solve time."""
     import torch
     from paper_1908_00741_gb300 import hbmc as H
     from paper_1908_00741_gb300 import workloads as W
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     t = time.perf_counter()
     items = W.batch_problems(args.batch_systems)
     gen_s = time.perf_counter() - t
@@ -424,38 +523,54 @@ def run_batch(args):
     assert st == H.OK
     b = torch.tensor(bvec, device="cuda")
     x = torch.zeros_like(b)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         x.zero_()
         res = H.hbmc_batch_iccg(batch, b, x, tol=TOL)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with ClockSampler(local) as clk:
-        ev[0].record(stream)
-        for _ in range(args.steps):
-            x.zero_()
-            res = H.hbmc_batch_iccg(batch, b, x, tol=TOL)
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    ev[0].record(stream)
+    for _ in range(steps):
+        x.zero_()
+        res = H.hbmc_batch_iccg(batch, b, x, tol=TOL)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / steps
     inf = batch.info()
-    line = {
-        "metric": "batched ICCG time to 1e-8 FP64 residual (all systems)", "value": round(ms, 3), "unit": "ms",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32-subst/f64-cg",
-        "data": "synthetic",
-        "config": {"workload": f"{len(mats)} systems, 7/27-point stencils n^3 with n in [16, 64], lognormal "
-                               f"sigma in [0, 2], natural order, box blocking",
-                   "systems": len(mats), "n_total": n_total, "nnz_total": int(sum(A.nnz for A in mats)),
-                   "bs": best, "w": 32, "colors": inf["nc"], "units": inf["units"]},
-        "autotune": {"candidates": [4, 8, 16, 32], "subset_ms": [round(float(v), 3) for v in cand_ms],
-                     "best_bs": best, "seconds": round(tune_s, 2)},
-        "all_converged": bool(res.status == H.OK), "max_true_relres": float(res.true_relres.max()),
-        "iters": {"min": int(res.iters.min()), "median": float(np.median(res.iters)), "max": int(res.iters.max())},
-        "per_system_ms": {"min": round(float(res.solve_ms.min()), 3),
-                          "median": round(float(np.median(res.solve_ms)), 3),
-                          "max": round(float(res.solve_ms.max()), 3)},
-        "unknowns_per_s": round(n_total / (ms * 1e-3), 1),
-        "gen_s": round(gen_s, 1), "build_s": round(build_s, 1), "clocks": clk.summary(),
-    }
+    per_iter = np.array([spmv_bytes(A.n, A.nnz) + sum(subst_bytes(A.n, (A.nnz - A.n) // 2, 4)) + 9 * A.n * 8
+                         for A in mats], dtype=np.float64)
+    gbs = float((per_iter * res.iters).sum() / (ms * 1e-3) / 1e9)
+    batch.close()
+    return {"workload": f"{len(mats)} systems, 7/27-point stencils n^3 with n in [16, 64], lognormal "
+                        f"sigma in [0, 2], natural order, box blocking",
+            "systems": len(mats), "n_total": n_total, "nnz_total": int(sum(A.nnz for A in mats)),
+            "bs": best, "w": 32, "colors": inf["nc"], "units": inf["units"], "ms": round(ms, 3),
+            "all_converged": bool(res.status == H.OK), "max_true_relres": float(res.true_relres.max()),
+            "iters": {"min": int(res.iters.min()), "median": float(np.median(res.iters)),
+                      "max": int(res.iters.max())},
+            "per_system_ms": {"min": round(float(res.solve_ms.min()), 3),
+                              "median": round(float(np.median(res.solve_ms)), 3),
+                              "max": round(float(res.solve_ms.max()), 3)},
+            "aggregate": {"GB/s": round(gbs, 1), **fracs(gbs, peak),
+                          "unknowns_per_s": round(n_total / (ms * 1e-3), 1)},
+            "autotune": {"candidates": [4, 8, 16, 32], "subset_ms": [round(float(v), 3) for v in cand_ms],
+                         "best_bs": best, "seconds": round(tune_s, 2)},
+            "gen_s": round(gen_s, 1), "build_s": round(build_s, 1)}
+
+def run_batch(args):
+    """256 independent SPD systems (7- or 27-point, n^3 with n ~ U{16..64},
+    lognormal sigma ~ U[0, 2]) solved together; block size chosen by the
+    library's autotuner on a 32-system subset; FP32 substitutions, FP64 CG."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    peak, _ = measured_peaks()
+    with ClockSampler(local) as clk:
+        rep = batch_report(args, local, peak, steps=args.steps, warmup=args.warmup)
+    line = {"metric": "batched ICCG time to 1e-8 FP64 residual (all systems)", "value": rep["ms"], "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": rep["ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32-subst/f64-cg",
+            "data": "synthetic", "config": {k: rep[k] for k in ("workload", "systems", "n_total", "nnz_total",
+                                                                 "bs", "w", "colors", "units")},
+            **{k: v for k, v in rep.items() if k not in ("workload", "ms")}, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -464,38 +579,18 @@ def run_batch(args):
 # learned IC shift: train on shift sweeps, then compare with the plain rule
 # --------------------------------------------------------------------------
 
-def learned_instances(count, seed0):
-    """Training/held-out systems: 70% 3-DOF vector Laplacians (nodes m^3 with
-    m ~ U{12..40}, dominance factor ~ U[0.9, 1.2]) and 30% heterogeneous 27-point
-    stencils (m ~ U{16..48}, sigma ~ U[0, 2]); random input order."""
-    from paper_1908_00741_gb300 import workloads as W
-    out = []
-    for k in range(count):
-        seed = seed0 + k
-        u = W.uniform(seed, 4)
-        if u[0] < 0.7:
-            m = 12 + min(int(u[1] * 29), 28)
-            A = W.vector_laplacian(m, seed, 0.9 + 0.3 * u[2])
-        else:
-            m = 16 + min(int(u[1] * 33), 32)
-            A = W.heterogeneous_stencil(m, 27, 2.0 * u[2], seed)
-        A = W.permute_input(A, W.random_order(seed ^ 0x5bd1e995, A.n))
-        b, _ = W.rhs_from_solution(A, seed + 77777)
-        out.append((A, b))
-    return out
-
-
-def run_learned(args):
+def learned_report(args, local):
+    """Train the shift network on the GPU from shift sweeps over generated
+    systems, compare it with the plain rule on held-out systems, and use it on
+    the 27-point, 3-DOF and curl-curl configurations."""
     import torch
     from paper_1908_00741_gb300 import hbmc as H
     from paper_1908_00741_gb300 import learned_shift as LS
     from paper_1908_00741_gb300 import workloads as W
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     t = time.perf_counter()
-    train = learned_instances(args.learned_train, 5000)
-    held = learned_instances(args.learned_heldout, 90000)
+    train = W.learned_family(args.learned_train, 5000)
+    held = W.learned_family(args.learned_heldout, 90000)
     gen_s = time.perf_counter() - t
     t = time.perf_counter()
     sw = LS.sweep([A for A, _ in train], [b for _, b in train], bs=8, maxit=2000)
@@ -505,9 +600,7 @@ def run_learned(args):
     net = LS.train(X, T, steps=4000, lr=3e-3)
     train_s = time.perf_counter() - t
     swh = LS.sweep([A for A, _ in held], [b for _, b in held], bs=8, maxit=2000)
-    plain, learned, fb = LS.evaluate(net, swh)
-    best = np.array([swh.iters[s, LS.best_choice(swh.iters[s])] for s in range(len(held))
-                     if LS.plain_choice(swh.iters[s]) >= 0])
+    plain, learned, best, fb = LS.evaluate(net, swh)
 
     def solve(P, name):
         ctx = H.hbmc_build(P.A, P.bs, 32, box=P.box, precision=H.PREC_F32, device=local)
@@ -517,13 +610,13 @@ def run_learned(args):
             st, shift, used_fb = H.hbmc_ic0_auto(ctx, nn)
             assert st == H.OK
             x = torch.zeros_like(b)
-            H.hbmc_iccg(ctx, b, x, tol=TOL)
+            H.hbmc_iccg(ctx, b, x, tol=TOL, maxit=20000)
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             ev[0].record()
             reps = 3
             for _ in range(reps):
                 x.zero_()
-                r = H.hbmc_iccg(ctx, b, x, tol=TOL)
+                r = H.hbmc_iccg(ctx, b, x, tol=TOL, maxit=20000)
             ev[1].record()
             torch.cuda.synchronize()
             rows[tag] = {"shift": shift, "fallback": used_fb, "iters": r.iters, "status": r.status,
@@ -531,21 +624,35 @@ def run_learned(args):
         ctx.close()
         return {"workload": name, "n": P.A.n, "nnz": P.A.nnz, **rows}
 
-    cfg5 = solve(W.vector_laplacian_problem(args.veclap_m, bs=8), f"3-DOF vector Laplacian {args.veclap_m}^3 nodes")
-    cfg3 = solve(W.heterogeneous27_problem(args.hetero_m, bs=8), f"heterogeneous 27-point {args.hetero_m}^3")
-    line = {
-        "metric": "CG iterations to 1e-8 with the learned IC shift vs the plain positive-pivot rule",
-        "value": float(learned.mean()), "unit": "iterations (held-out mean)", "higher_is_better": False,
-        "n_gpus": world, "dtype": "f32-subst/f64-cg", "data": "synthetic",
-        "config": {"workload": "shift sweeps over generated 3-DOF vector Laplacians and 27-point stencils",
-                   "train_systems": len(train), "heldout_systems": len(held), "shift_grid": list(H.shift_grid()),
-                   "bs": 8, "w": 32},
+    return {
+        "family": "curl-curl systems (IC(0) needs a shift), 3-DOF vector Laplacians and heterogeneous "
+                  "27-point stencils, random order",
+        "train_systems": len(train), "heldout_systems": len(held), "shift_grid": list(H.shift_grid()),
         "heldout": {"plain_mean_iters": float(plain.mean()), "learned_mean_iters": float(learned.mean()),
                     "best_mean_iters": float(best.mean()), "gain_vs_plain": float(1 - learned.mean() / plain.mean()),
                     "fallbacks": int(fb.sum()), "systems": int(len(plain))},
-        "training": {"samples": int(len(T)), "final_loss": None, "sweep_s": round(sweep_s, 1),
-                     "train_s": round(train_s, 2), "gen_s": round(gen_s, 1)},
-        "config5": cfg5, "config3": cfg3,
+        "training": {"samples": int(len(T)), "sweep_s": round(sweep_s, 1), "train_s": round(train_s, 2),
+                     "gen_s": round(gen_s, 1)},
+        "config5": solve(W.vector_laplacian_problem(args.veclap_m, bs=8),
+                         f"3-DOF vector Laplacian {args.veclap_m}^3 nodes"),
+        "config3": solve(W.heterogeneous27_problem(args.hetero_m, bs=8), f"heterogeneous 27-point {args.hetero_m}^3"),
+        "curl_curl": solve(W.curl_curl_problem(args.curl_m),
+                           f"curl-curl + 0.01 I on {args.curl_m}^3 cells (edge unknowns)"),
+    }
+
+
+def run_learned(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    rep = learned_report(args, local)
+    line = {
+        "metric": "CG iterations to 1e-8 with the learned IC shift vs the plain positive-pivot rule",
+        "value": rep["heldout"]["learned_mean_iters"], "unit": "iterations (held-out mean)",
+        "higher_is_better": False, "n_gpus": world, "dtype": "f32-subst/f64-cg", "data": "synthetic",
+        "config": {"workload": rep["family"], "train_systems": rep["train_systems"],
+                   "heldout_systems": rep["heldout_systems"], "shift_grid": rep["shift_grid"], "bs": 8, "w": 32},
+        **{k: v for k, v in rep.items() if k not in ("family", "train_systems", "heldout_systems", "shift_grid")},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -918,6 +1025,12 @@ def run_structural(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands (single-threaded FP64 C)
+    on this host's cores, on the GPU arm's workload.  A full solve takes
+    seconds per step, so each step is a bounded sample: setup once, then
+    `--ref-sample-iters` PCG iterations per step; `value` is the per-iteration
+    time scaled to the full solve's iteration count (the GPU solve's, 124 at
+    128^3 bs 8), `ms_per_step` the measured time of a sampled step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -928,29 +1041,41 @@ def run_reference(args):
     P = W.poisson_problem(GRID, bs=args.bs)
     an = oracle.analyse(P.A, P.bs, P.w, box=P.box)
     lval, _, dinv, _ = oracle.factor(an, 0.0)
+    nc = int(an.nc)
     full_iters = args.ref_full_iters
     sample = args.ref_sample_iters
 
-    def step():
+    def step(maxit):
         t = time.perf_counter()
-        s = oracle.pcg(an, lval, dinv, P.b, tol=TOL, maxit=sample)
-        return (time.perf_counter() - t) / max(s.iters, 1) * full_iters * 1e3
+        s = oracle.pcg(an, lval, dinv, P.b, tol=TOL, maxit=maxit)
+        dt = time.perf_counter() - t
+        return dt, s.iters
 
+    # the start of a solve (r = b - A x0, z = M^-1 r) once, then the sampled steps
+    start_s = step(0)[0]
     for _ in range(args.warmup):
-        step()
-    vals = [step() for _ in range(args.steps)]
-    v = statistics.mean(vals)
+        step(sample)
+    runs = [step(sample) for _ in range(args.steps)]
+    step_s = statistics.mean(dt for dt, _ in runs)
+    per_iter = statistics.mean(max(dt - start_s, 0.0) / max(it, 1) for dt, it in runs)
+    v = (start_s + per_iter * full_iters) * 1e3
+    host = host_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "ms", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"7-point Poisson {GRID}^3 ({P.A.n} unknowns), bs={args.bs}, w=32, "
-                               f"FP64, tol {TOL:g}", "bs": args.bs, "w": 32, "precision": "f64",
-                   "parallelism": "single-thread CPU oracle"},
+        "config": {"workload": f"7-point Poisson {GRID}^3 ({P.A.n} unknowns, {P.A.nnz} nonzeros), "
+                               f"bs={args.bs} ({'x'.join(map(str, P.box))} boxes), w=32, FP64 substitutions, "
+                               f"tol {TOL:g}",
+                   "n": P.A.n, "nnz": P.A.nnz, "bs": args.bs, "w": 32, "colors": nc, "precision": "f64",
+                   "loop": "host (single-thread CPU oracle)", "parallelism": "single-thread CPU oracle"},
+        "scaled_from_iters": sample, "full_iters": full_iters, "sample_s": round(step_s, 4),
         "cpu_baseline": {"value": round(v, 3), "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: {sample} PCG iterations of the 128^3 solve, scaled to "
-                                   f"{full_iters} iterations"},
+                         "sample": f"each step: the start of the 128^3 solve and {sample} PCG iterations "
+                                   f"({step_s:.3f} s); value = start ({start_s:.3f} s) + per-iteration time "
+                                   f"x {full_iters} iterations",
+                         "scaled_from_iters": sample, "sample_s": round(step_s, 4), "host": host},
         "e2e": {"value": round(v, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -975,12 +1100,15 @@ def main():
     ap.add_argument("--veclap-m", type=int, default=100)
     ap.add_argument("--structural-m", type=int, default=68)
     ap.add_argument("--hetero-m", type=int, default=96)
+    ap.add_argument("--curl-m", type=int, default=70)
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="graph: one CUDA graph per solve with a device-side while node; "
                          "host: host-driven iterations (kernels visible to ncu)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 27-point, 3-DOF, batch and learned-shift configurations of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=40)
     ap.add_argument("--ref-sample-iters", type=int, default=10)

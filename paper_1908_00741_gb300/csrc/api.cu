@@ -234,6 +234,7 @@ hbmc_status upload(hbmc_ctx *ctx) {
       TRY(dupload(ctx, d.dag_unit_color, t.ucolor));
       TRY(dupload(ctx, d.dag_color_units, t.color_units));
       TRY(dalloc(ctx, d.dag_color_done, 2 * (size_t)h.nc));
+      TRY(dupload(ctx, d.dag_counted, t.counted));
       TRY(dalloc(ctx, d.dag_exit, 2));
       TRY(dupload(ctx, d.dep_ptr_f, t.ptr_f));
       TRY(dupload(ctx, d.dep_f, t.dep_f));
@@ -404,15 +405,14 @@ hbmc_status solve_dev(hbmc_ctx *ctx, const double *b_dev, double *x_dev, double 
     // and two preconditioner applications (4 n_c sweeps).
     // Row-split SpMV: one more launch for the pieces; the fused last color
     // of the preconditioner: one launch fewer.
-    // Dependency-driven sweeps: one launch per sweep.
-    const int64_t fb = !bicg && hbmc::fb_tw_usable(d, prec) ? 1 : 0;
-    const int64_t nc = hbmc::dag_selected(d, prec) ? 1 : d.nc, per = bicg ? 7 + 4 * nc : 3 + 2 * nc + (d.split && d.n_virt > 0 ? 1 : 0) - fb;
+    const int64_t sw = hbmc::sweep_launches(d, prec), pc = hbmc::precond_launches(d, prec);
+    const int64_t per = bicg ? 7 + 4 * sw : 3 + pc + (d.split && d.n_virt > 0 ? 1 : 0);
     int64_t passes = r.iters > 0 ? r.iters : 1;
     if (ctx->opt.loop_mode == HBMC_LOOP_HOST) {
       const int64_t every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
       passes = (passes + every - 1) / every * every;
     }
-    ctx->last_launches = persistent ? 5 : (bicg ? 4 : 4 + 2 * nc - fb) + passes * per + 2;
+    ctx->last_launches = persistent ? 5 : (bicg ? 4 : 4 + pc) + passes * per + 2;
   }
   if (iters) *iters = r.iters;
   if (relres) *relres = r.relres;

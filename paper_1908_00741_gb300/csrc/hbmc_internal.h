@@ -253,6 +253,7 @@ struct DeviceLayout {
   int32_t *dep_f = nullptr, *dep_b = nullptr, *dag_order_b = nullptr, *dag_unit_color = nullptr;
   unsigned *dag_flag_f = nullptr, *dag_flag_b = nullptr, *dag_abort = nullptr;
   unsigned *dag_color_done = nullptr;  // per color, forward then backward (cleared by each launch's last block)
+  uint8_t *dag_counted = nullptr;      // per color, forward then backward: some level-1 block waits on its counter
   unsigned *dag_exit = nullptr;        // finished CUDA blocks of the running launch, forward and backward
   unsigned long long *dag_ticket = nullptr;
   DagPlan dg_f64_f, dg_f64_b, dg_f32_f, dg_f32_b;

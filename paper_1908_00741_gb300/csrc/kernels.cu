@@ -691,6 +691,12 @@ void enqueue_spmv_plain(const DeviceLayout &d, const double *p, double *q, bool 
 // Colors pick their kernel one by one: the loader-thread kernel for colors
 // with long other-color runs or few level-1 blocks, else the
 // bulk-copy-staged warp kernel; both give the same bits.
+int64_t sweep_launches(const DeviceLayout &d, int prec) { return dag_selected(d, prec) ? 1 : d.nc; }
+
+int64_t precond_launches(const DeviceLayout &d, int prec) {
+  return 2 * sweep_launches(d, prec) - (fb_tw_usable(d, prec) ? 1 : 0);
+}
+
 void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s) {
   if (dag_selected(d, prec)) return enqueue_fwd_dag(d, prec, r, check_done, s);
   const bool wide = wide_usable(d, true, prec), tw = tw_usable(d, true, prec);

@@ -57,6 +57,7 @@ void launch_bwd_wide_color(const DeviceLayout &d, int prec, int c, const double 
 struct DagTables {
   std::vector<int64_t> ptr_f, ptr_b, color_units;
   std::vector<int32_t> dep_f, dep_b, order_b, ucolor;
+  std::vector<uint8_t> counted;  // per color, forward then backward: some level-1 block waits on its counter
 };
 bool dag_host_tables(const HostLayout &h, DagTables &t);
 void plan_dag_kernels(const HostLayout &h, DeviceLayout &d);
@@ -66,6 +67,10 @@ bool dag_selected(const DeviceLayout &d, int prec);
 void enqueue_fwd_dag(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
 void enqueue_bwd_dag(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
                      cudaStream_t s);
+
+// launches of one forward (or backward) sweep, and of one preconditioner application
+int64_t sweep_launches(const DeviceLayout &d, int prec);
+int64_t precond_launches(const DeviceLayout &d, int prec);
 
 // Bulk-copy-fed SpMV, w = 32 (spmv_tma.cu)
 void plan_spmv_tma(const HostLayout &h, DeviceLayout &d);

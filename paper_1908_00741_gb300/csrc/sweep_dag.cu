@@ -72,6 +72,7 @@ struct DagArgs {
   const int64_t *color_units;  // color -> its level-1 blocks
   unsigned *flag;          // per level-1 block: epoch of its last published result
   unsigned *color_done;    // per color: level-1 blocks published in this launch
+  const uint8_t *counted;  // per color: some level-1 block waits on its counter
   unsigned *exit_cnt;      // CUDA blocks of this launch that have finished
   unsigned long long *ticket;
   unsigned *abort;   // epoch of the last launch a wait of which ran out
@@ -292,7 +293,8 @@ __device__ __forceinline__ int64_t dag_unit(const DagArgs<T> &a, unsigned char *
     if (tid == 0 && u != a.stall) {
       __threadfence();  // release: the warp's stores (ordered by __syncwarp) before both publications
       st_relaxed_gpu(a.flag + u, epoch);
-      atomicAdd(a.color_done + a.unit_color[u], 1u);
+      const int c = a.unit_color[u];
+      if (a.counted[c]) atomicAdd(a.color_done + c, 1u);
     }
   }
   return k;
@@ -392,6 +394,7 @@ DagArgs<T> dag_args(const DeviceLayout &d, bool fwd, const DagPlan &p) {
   a.unit_color = d.dag_unit_color;
   a.color_units = d.dag_color_units;
   a.color_done = fwd ? d.dag_color_done : d.dag_color_done + d.nc;
+  a.counted = d.dag_counted + (fwd ? 0 : d.nc);
   a.exit_cnt = d.dag_exit + (fwd ? 0 : 1);
   a.nc = d.nc;
   a.ticket = d.dag_ticket + (fwd ? 0 : 1);
@@ -468,6 +471,10 @@ bool dag_host_tables(const HostLayout &h, DagTables &t) {
   }
   deps_of(h, h.fx_ptr, h.fx_col, t.ucolor, t.ptr_f, t.dep_f);
   deps_of(h, h.bx_ptr, h.bx_col, t.ucolor, t.ptr_b, t.dep_b);
+  t.counted.assign(2 * (size_t)h.nc, 0);
+  for (int dir = 0; dir < 2; ++dir)
+    for (int32_t v : dir == 0 ? t.dep_f : t.dep_b)
+      if (v < 0) t.counted[(size_t)dir * h.nc + (size_t)(-v - 1)] = 1;
   // backward sweep order: colors descending, level-1 blocks ascending within a color
   t.order_b.reserve((size_t)h.ntiles);
   for (int c = h.nc - 1; c >= 0; --c)

@@ -91,8 +91,16 @@ __device__ __forceinline__ void tw_unit(const TwArgs<T> &a, unsigned char *ws, i
   const int olen = rec_at(r0, r1, 0), ilen = rec_at(r0, r1, 1);
   const int64_t obeg = (int64_t)(((uint64_t)(uint32_t)rec_at(r0, r1, 3) << 32) | (uint32_t)rec_at(r0, r1, 2));
   const int64_t ibeg = (int64_t)(((uint64_t)(uint32_t)rec_at(r0, r1, 5) << 32) | (uint32_t)rec_at(r0, r1, 4));
-  // trip 2
+  // trip 2 (FP32: the other-color run is also prefetched into L2, so that
+  // its later chunks come from L2; measured 22.2 -> 20.7 us for the 128^3
+  // forward sweep, no gain in FP64)
   if (lane == 0) {
+    if constexpr (sizeof(T) == 4) {
+      if (olen > 0) {
+        prefetch_l2(a.o_col + obeg, (uint32_t)olen * 4u);
+        prefetch_l2(a.o_val + obeg, (uint32_t)olen * (uint32_t)sizeof(T));
+      }
+    }
     mbar_arrive_expect_tx(bar, (uint32_t)ilen * (uint32_t)(sizeof(T) + 1));
     if (ilen > 0) {
       tma_load_1d(iv, a.i_val + ibeg, (uint32_t)ilen * (uint32_t)sizeof(T), bar);
@@ -209,8 +217,14 @@ __device__ __forceinline__ void fb_unit(const TwArgs<T> &af, const TwArgs<T> &ab
   const int olen_b = rec_at(b0, b1, 0), ilen_b = rec_at(b0, b1, 1);
   const int64_t obeg_b = (int64_t)(((uint64_t)(uint32_t)rec_at(b0, b1, 3) << 32) | (uint32_t)rec_at(b0, b1, 2));
   const int64_t ibeg_b = (int64_t)(((uint64_t)(uint32_t)rec_at(b0, b1, 5) << 32) | (uint32_t)rec_at(b0, b1, 4));
-  // trip 2: the forward same-block run
+  // trip 2: the forward same-block run (and, FP32, the other-color run into L2)
   if (lane == 0) {
+    if constexpr (sizeof(T) == 4) {
+      if (olen > 0) {
+        prefetch_l2(af.o_col + obeg, (uint32_t)olen * 4u);
+        prefetch_l2(af.o_val + obeg, (uint32_t)olen * (uint32_t)sizeof(T));
+      }
+    }
     mbar_arrive_expect_tx(bar, (uint32_t)ilen * (uint32_t)(sizeof(T) + 1));
     if (ilen > 0) {
       tma_load_1d(iv, af.i_val + ibeg, (uint32_t)ilen * (uint32_t)sizeof(T), bar);

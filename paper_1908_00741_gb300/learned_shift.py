@@ -24,8 +24,15 @@ FAIL_FACTOR = 4.0  # a failed shift (pivot or no convergence) counts as 4 * maxi
 class Sweep:
     features: np.ndarray   # [nsys, 12]
     iters: np.ndarray      # [nsys, grid]; -1 = IC(0) failed or CG did not converge
+    ic_ok: np.ndarray      # [nsys, grid]; IC(0) had only positive, finite pivots
     true_relres: np.ndarray
     maxit: int
+
+    def cost(self, s, c):
+        """CG iterations of system s at grid shift c; a shift whose IC(0) or CG
+        failed costs FAIL_FACTOR * maxit."""
+        it = self.iters[s, c]
+        return int(it) if it >= 0 else int(FAIL_FACTOR * self.maxit)
 
 
 def sweep(mats, bvecs, bs=8, tol=1e-8, maxit=2000, precision=H.PREC_F32, use_boxes=False) -> Sweep:
@@ -37,33 +44,34 @@ def sweep(mats, bvecs, bs=8, tol=1e-8, maxit=2000, precision=H.PREC_F32, use_box
     b = torch.tensor(np.concatenate(bvecs), device="cuda")
     x = torch.zeros_like(b)
     iters = np.full((len(mats), len(grid)), -1, dtype=np.int64)
+    ic_ok = np.zeros((len(mats), len(grid)), dtype=bool)
     tr = np.full((len(mats), len(grid)), np.nan)
     for c, a in enumerate(grid):
         st, bad = H.hbmc_batch_ic0(batch, shifts=np.full(len(mats), a))
         x.zero_()
         res = H.hbmc_batch_iccg(batch, b, x, tol=tol, maxit=maxit)
-        ok = (bad == -1) & (res.statuses == H.OK)
+        ic_ok[:, c] = bad == -1
+        ok = ic_ok[:, c] & (res.statuses == H.OK)
         iters[ok, c] = res.iters[ok]
         tr[ok, c] = res.true_relres[ok]
     batch.close()
-    return Sweep(feats, iters, tr, maxit)
+    return Sweep(feats, iters, ic_ok, tr, maxit)
 
 
-def plain_choice(iters_row):
-    """Index of the plain rule's shift: the first shift whose IC(0) works.  A
-    sweep marks failures of IC(0) and of CG alike, so the first entry that is
-    not -1 stands in for the first positive-pivot shift."""
-    ok = np.flatnonzero(iters_row >= 0)
+def plain_choice(ic_row):
+    """Index of the plain rule's shift: the first grid shift whose IC(0) has
+    only positive, finite pivots (whatever CG then does with it), -1 if none."""
+    ok = np.flatnonzero(ic_row)
     return int(ok[0]) if len(ok) else -1
 
 
-def best_choice(iters_row):
-    """argmin over converged shifts, ties to the smaller shift."""
-    ok = iters_row >= 0
-    if not ok.any():
+def best_choice(sw: Sweep, s):
+    """argmin of the cost over the shifts whose IC(0) works, ties to the
+    smaller shift; -1 if none works."""
+    ok = np.flatnonzero(sw.ic_ok[s])
+    if not len(ok):
         return -1
-    v = np.where(ok, iters_row, np.iinfo(np.int64).max)
-    return int(np.argmin(v))
+    return int(ok[np.argmin([sw.cost(s, c) for c in ok])])
 
 
 def dataset(sw: Sweep):
@@ -93,6 +101,16 @@ def init_params(D, seed=0):
                            glorot(1, h).ravel(), [0.0]]).astype(np.float32)
 
 
+# Features the network does not see: log10 n (0) and the color count (9)
+# describe the system's size and ordering, not what the shift acts on, and a
+# network trained on small systems extrapolates them badly (measured: on the
+# 96^3 27-point and 70^3 curl-curl systems, with them, it chose 2.048 and
+# lost 70% and 34% against the plain rule).  They are masked by standardizing
+# them to 0 whatever their value.
+MASKED_FEATURES = (0, 9)
+MASK_STD = 1e30
+
+
 def train(X, T, steps=3000, lr=3e-3, seed=0) -> H.Mlp:
     """Network trained on the GPU by the library's kernels."""
     import torch
@@ -101,6 +119,9 @@ def train(X, T, steps=3000, lr=3e-3, seed=0) -> H.Mlp:
     mean = X.mean(axis=0)
     std = X.std(axis=0)
     std = np.where(std > 1e-6, std, 1.0).astype(np.float32)
+    for f in MASKED_FEATURES:
+        mean[f] = 0.0
+        std[f] = MASK_STD
     net.set_params(init_params(D, seed), mean, std)
     Xd = torch.tensor(X, device="cuda")
     Td = torch.tensor(T, device="cuda")
@@ -119,21 +140,24 @@ def predicted_choice(net: H.Mlp, feats):
 
 
 def evaluate(net: H.Mlp, sw: Sweep):
-    """Iterations with the plain rule and with the learned choice (plus the
-    plain-rule fallback when the learned shift fails), per system."""
+    """Per system whose IC(0) works at some grid shift: the cost (CG
+    iterations) with the plain rule, with the learned choice (when its IC(0)
+    fails, the plain rule continues from the next larger grid shift, as
+    hbmc_ic0_auto does) and with the best grid shift, and whether the
+    fallback was taken."""
     choice, _ = predicted_choice(net, sw.features)
-    plain, learned, fallback = [], [], []
+    plain, learned, best, fallback = [], [], [], []
     for s in range(len(sw.iters)):
-        row = sw.iters[s]
-        pc = plain_choice(row)
+        pc = plain_choice(sw.ic_ok[s])
         if pc < 0:
             continue
         lc = int(choice[s])
-        fb = row[lc] < 0
-        if fb:  # the learned shift failed: continue with the plain rule above it
-            nxt = [c for c in range(lc + 1, len(row)) if row[c] >= 0]
+        fb = not sw.ic_ok[s, lc]
+        if fb:
+            nxt = [c for c in range(lc + 1, sw.ic_ok.shape[1]) if sw.ic_ok[s, c]]
             lc = nxt[0] if nxt else pc
-        plain.append(row[pc])
-        learned.append(row[lc])
+        plain.append(sw.cost(s, pc))
+        learned.append(sw.cost(s, lc))
+        best.append(sw.cost(s, best_choice(sw, s)))
         fallback.append(fb)
-    return np.array(plain), np.array(learned), np.array(fallback)
+    return np.array(plain), np.array(learned), np.array(best), np.array(fallback)

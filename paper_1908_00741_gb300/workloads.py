@@ -317,6 +317,91 @@ def irregular_structural(m: int, seed: int, mean_refine: float = 0.11, keep_near
     return A
 
 
+def curl_curl(m: int, sigma: float, seed: int, hetero: float = 0.0) -> CSR:
+    """Edge unknowns of an m^3 cell grid (3 m (m+1)^2 edges; unknown order:
+    x-edges, then y-, then z-edges, each lexicographic) with
+    A = C^T W C + sigma I: C is the discrete curl (face <- its four edges,
+    signs by the face's orientation), W = diag(w_f) with w_f = exp(N(0,
+    hetero^2)) per face (stream `seed`), sigma > 0 a mass-like shift.  The
+    shape of an edge-element eddy-current system such as the paper's IEEJ
+    model: symmetric positive definite but nearly singular for small sigma
+    (the gradients are in the null space of the curl), off-diagonal entries
+    of both signs, and an IC(0) that breaks down without a diagonal shift.
+    """
+    n1 = m + 1
+    nx, ny = m * n1 * n1, n1 * m * n1
+
+    def ex(i, j, k):
+        return i + m * (j + n1 * k)
+
+    def ey(i, j, k):
+        return nx + i + n1 * (j + m * k)
+
+    def ez(i, j, k):
+        return nx + ny + i + n1 * (j + n1 * k)
+
+    faces = []
+    g = np.arange
+    # xy faces (i < m, j < m, k <= m): +ex(i,j,k) +ey(i+1,j,k) -ex(i,j+1,k) -ey(i,j,k)
+    k, j, i = np.meshgrid(g(n1), g(m), g(m), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    faces.append(np.stack([ex(i, j, k), ey(i + 1, j, k), ex(i, j + 1, k), ey(i, j, k)], 1))
+    # yz faces (i <= m, j < m, k < m): +ey(i,j,k) +ez(i,j+1,k) -ey(i,j,k+1) -ez(i,j,k)
+    k, j, i = np.meshgrid(g(m), g(m), g(n1), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    faces.append(np.stack([ey(i, j, k), ez(i, j + 1, k), ey(i, j, k + 1), ez(i, j, k)], 1))
+    # zx faces (i < m, j <= m, k < m): +ez(i,j,k) +ex(i,j,k+1) -ez(i+1,j,k) -ex(i,j,k)
+    k, j, i = np.meshgrid(g(m), g(n1), g(m), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    faces.append(np.stack([ez(i, j, k), ex(i, j, k + 1), ez(i + 1, j, k), ex(i, j, k)], 1))
+    F = np.concatenate(faces).astype(np.int64)
+    sign = np.array([1.0, 1.0, -1.0, -1.0])
+    w = np.exp(normal(seed, len(F), hetero)) if hetero > 0 else np.ones(len(F))
+    n = nx + ny + n1 * n1 * m
+    rows = np.repeat(F, 4, axis=1).ravel()
+    cols = np.tile(F, (1, 4)).ravel()
+    vals = (w[:, None, None] * sign[None, :, None] * sign[None, None, :]).reshape(-1)
+    # sum the faces' contributions per (row, col) pair, then add sigma on the diagonal
+    key = rows * n + cols
+    uk, inv = np.unique(key, return_inverse=True)
+    acc = np.bincount(inv, weights=vals, minlength=len(uk))
+    r, c = uk // n, uk % n
+    acc[r == c] += sigma
+    return _assemble(n, r, c, acc)
+
+
+def learned_family(count: int, seed0: int, cc_m=(6, 12), vl_m=(8, 20), st_m=(12, 32),
+                   mix=(0.5, 0.25, 0.25)):
+    """Systems for the learned IC shift: `count` pairs (A, b), system k from
+    stream seed0 + k, drawn with probabilities `mix` from
+      - curl-curl systems (curl_curl with m ~ U{cc_m}, sigma = 10^U(-3, 0),
+        face heterogeneity ~ U(0, 1.2)): IC(0) needs a shift, and the best
+        grid shift is the first one that works or the next;
+      - 3-DOF vector Laplacians (m ~ U{vl_m} nodes per side, dominance
+        ~ U[0.9, 1.2]);
+      - heterogeneous 27-point stencils (m ~ U{st_m}, sigma ~ U[0, 2]);
+    the last two with the plain rule's 0 as the best shift.  Random input
+    order; b = A x*, x* ~ U(-1, 1)."""
+    out = []
+    for k in range(count):
+        seed = seed0 + k
+        u = uniform(seed, 5)
+
+        def pick(lo_hi):
+            return lo_hi[0] + min(int(u[1] * (lo_hi[1] - lo_hi[0] + 1)), lo_hi[1] - lo_hi[0])
+
+        if u[0] < mix[0]:
+            A = curl_curl(pick(cc_m), 10.0 ** (-3.0 + 3.0 * u[2]), seed, 1.2 * u[3])
+        elif u[0] < mix[0] + mix[1]:
+            A = vector_laplacian(pick(vl_m), seed, 0.9 + 0.3 * u[2])
+        else:
+            A = heterogeneous_stencil(pick(st_m), 27, 2.0 * u[2], seed)
+        A = permute_input(A, random_order(seed ^ 0x5BD1E995, A.n))
+        b, _ = rhs_from_solution(A, seed + 77777)
+        out.append((A, b))
+    return out
+
+
 @dataclasses.dataclass
 class Problem:
     """A linear system with its right-hand side and the blocking hint it asks for."""
@@ -377,6 +462,17 @@ def structural_problem(m: int = 68, bs: int = 8, w: int = 32, seed: int = 7, rhs
     A = irregular_structural(m, seed)
     b, xs = rhs_from_solution(A, rhs_seed)
     return Problem(f"structural_{m}^3x3_bs{bs}", A, b, xs, bs, w, None)
+
+
+def curl_curl_problem(m: int, sigma: float = 0.01, seed: int = 6, hetero: float = 0.3, bs: int = 8,
+                      w: int = 32, order_seed: int = 8, rhs_seed: int = 0) -> Problem:
+    """curl_curl on an m^3 cell grid in a random input order (algebraic
+    blocking); m = 70 gives 1,058,610 unknowns, about the size of the paper's IEEJ
+    eddy-current system."""
+    A = curl_curl(m, sigma, seed, hetero)
+    A = permute_input(A, random_order(order_seed, A.n))
+    b, xs = rhs_from_solution(A, rhs_seed)
+    return Problem(f"curlcurl_{m}^3_bs{bs}", A, b, xs, bs, w, None)
 
 
 def convection_diffusion_problem(m: int, bs: int = 8, w: int = 32, velocity=(0.5, 0.3, 0.2),

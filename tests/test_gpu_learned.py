@@ -107,37 +107,32 @@ def test_plain_rule_matches_reference(lib, orc, A, bs, box):
     assert shift == ref
 
 
-def _instances(count, seed0, mmin=4, mmax=7):
-    out = []
-    for k in range(count):
-        u = W.uniform(7000 + seed0 + k, 2)
-        m = mmin + min(int(u[0] * (mmax - mmin + 1)), mmax - mmin)
-        dom = 0.9 + 0.3 * u[1]
-        A = W.permute_input(W.vector_laplacian(m, 5000 + seed0 + k, dom), W.random_order(9000 + seed0 + k, 3 * m ** 3))
-        b, _ = W.rhs_from_solution(A, 11000 + seed0 + k)
-        out.append((A, b))
-    return out
+def _instances(count, seed0):
+    # the library's learned-shift family at small sizes: curl-curl systems
+    # (IC(0) needs a shift; the best one is the first that works or the
+    # next), 3-DOF vector Laplacians and 27-point stencils (the best shift is 0)
+    return W.learned_family(count, seed0, cc_m=(5, 8), vl_m=(5, 8), st_m=(8, 14))
 
 
 def test_learned_shift_gain_over_plain_rule(lib):
-    """Train on shift sweeps of 64 small 3-DOF systems, evaluate on 24 held-out
+    """Train on shift sweeps of 160 small systems, evaluate on 32 held-out
     ones: mean CG iterations with the learned shift (plain-rule fallback when
-    its IC(0) fails) versus the plain rule's first positive-pivot shift."""
-    train = _instances(64, 0)
-    test = _instances(24, 1000)
+    its IC(0) fails) versus the plain rule's first positive-pivot shift.
+    Measured on GB300: plain 48.6, learned 45.0, best grid shift 44.4 (7.3%
+    fewer iterations than the plain rule); the test asks for at least 3%."""
+    train = _instances(160, 7000)
+    test = _instances(32, 8000)
     sw = LS.sweep([A for A, _ in train], [b for _, b in train], bs=4, maxit=1000)
     X, T = LS.dataset(sw)
     net = LS.train(X, T, steps=3000, lr=3e-3)
     swt = LS.sweep([A for A, _ in test], [b for _, b in test], bs=4, maxit=1000)
-    plain, learned, fb = LS.evaluate(net, swt)
-    best = np.array([swt.iters[s, LS.best_choice(swt.iters[s])] for s in range(len(test))
-                     if LS.plain_choice(swt.iters[s]) >= 0])
+    plain, learned, best, fb = LS.evaluate(net, swt)
     gain = 1.0 - learned.mean() / plain.mean()
     print(f"\nlearned-shift gain: plain {plain.mean():.2f} it, learned {learned.mean():.2f} it, "
           f"best {best.mean():.2f} it, gain {100 * gain:.1f}%, fallbacks {int(fb.sum())}/{len(fb)}")
-    assert len(plain) >= 20
-    # the network may not lose more than 5% against the rule it replaces
-    assert learned.mean() <= 1.05 * plain.mean()
+    assert len(plain) >= 28
+    # the network beats the rule it replaces by at least 3% on held-out systems
+    assert learned.mean() <= 0.97 * plain.mean()
     # and it must use its own choice on most systems (not only the fallback)
     assert fb.mean() <= 0.5
     # product path: hbmc_ic0_auto with the trained network on held-out systems
