@@ -117,5 +117,10 @@ def test_sequential_dot_within_bound_of_exact(orc, a, seed):
         fractions.Fraction(2.0 ** -1074)
     u = 2.0 ** -53
     k = len(a)
-    bound = k * u / (1 - k * u) * float(np.sum(np.abs(a * b)))
-    assert abs(fractions.Fraction(seq) - true) <= fractions.Fraction(bound)
+    # recursive summation of k products: relative error gamma_k = k u / (1 - k u)
+    # of sum |a_i b_i|, plus, where products or partial sums fall below the
+    # normal range, an absolute error of at most half the smallest subnormal
+    # (2^-1075) per rounding, 2k roundings
+    bound = fractions.Fraction(k * u / (1 - k * u)) * sum(abs(fractions.Fraction(float(x)) * fractions.Fraction(float(y)))
+                                                         for x, y in zip(a, b)) + 2 * k * fractions.Fraction(2.0 ** -1075)
+    assert abs(fractions.Fraction(seq) - true) <= bound
