@@ -512,10 +512,11 @@ def batch_report(args, local, peak, steps=3, warmup=2):
     sub = mats[:32]
     bsub = torch.tensor(np.concatenate([b for _, b, _ in items[:32]]), device="cuda")
     t = time.perf_counter()
-    best, cand_ms = H.hbmc_batch_autotune(sub, bsub, (4, 8, 16, 32), precision=H.PREC_F32, tol=TOL)
+    bs_cand, w_cand = (4, 8, 16, 32), (16, 32)
+    best, best_w, cand_ms = H.hbmc_batch_autotune_w(sub, bsub, bs_cand, w_cand, precision=H.PREC_F32, tol=TOL)
     tune_s = time.perf_counter() - t
     t = time.perf_counter()
-    batch = H.hbmc_batch_build(mats, best, precision=H.PREC_F32, device=local)
+    batch = H.hbmc_batch_build(mats, best, w=best_w, precision=H.PREC_F32, device=local)
     build_s = time.perf_counter() - t
     stream = torch.cuda.current_stream()
     H.hbmc_batch_set_stream(batch, stream)
@@ -542,7 +543,7 @@ def batch_report(args, local, peak, steps=3, warmup=2):
     return {"workload": f"{len(mats)} systems, 7/27-point stencils n^3 with n in [16, 64], lognormal "
                         f"sigma in [0, 2], natural order, box blocking",
             "systems": len(mats), "n_total": n_total, "nnz_total": int(sum(A.nnz for A in mats)),
-            "bs": best, "w": 32, "colors": inf["nc"], "units": inf["units"], "ms": round(ms, 3),
+            "bs": best, "w": best_w, "colors": inf["nc"], "units": inf["units"], "ms": round(ms, 3),
             "all_converged": bool(res.status == H.OK), "max_true_relres": float(res.true_relres.max()),
             "iters": {"min": int(res.iters.min()), "median": float(np.median(res.iters)),
                       "max": int(res.iters.max())},
@@ -551,8 +552,10 @@ def batch_report(args, local, peak, steps=3, warmup=2):
                               "max": round(float(res.solve_ms.max()), 3)},
             "aggregate": {"GB/s": round(gbs, 1), **fracs(gbs, peak),
                           "unknowns_per_s": round(n_total / (ms * 1e-3), 1)},
-            "autotune": {"candidates": [4, 8, 16, 32], "subset_ms": [round(float(v), 3) for v in cand_ms],
-                         "best_bs": best, "seconds": round(tune_s, 2)},
+            "autotune": {"subset": "the first 32 systems", "bs": list(bs_cand), "w": list(w_cand),
+                         "subset_ms": {f"bs{b}_w{w}": round(float(cand_ms[i, j]), 3)
+                                       for i, b in enumerate(bs_cand) for j, w in enumerate(w_cand)},
+                         "best_bs": best, "best_w": best_w, "slice_height": "w", "seconds": round(tune_s, 2)},
             "gen_s": round(gen_s, 1), "build_s": round(build_s, 1)}
 
 def run_batch(args):
@@ -593,13 +596,13 @@ def learned_report(args, local):
     held = W.learned_family(args.learned_heldout, 90000)
     gen_s = time.perf_counter() - t
     t = time.perf_counter()
-    sw = LS.sweep([A for A, _ in train], [b for _, b in train], bs=8, maxit=2000)
+    sw = LS.sweep([A for A, _ in train], [b for _, b in train], bs=8, maxit=3000)
     X, T = LS.dataset(sw)
     sweep_s = time.perf_counter() - t
     t = time.perf_counter()
     net = LS.train(X, T, steps=4000, lr=3e-3)
     train_s = time.perf_counter() - t
-    swh = LS.sweep([A for A, _ in held], [b for _, b in held], bs=8, maxit=2000)
+    swh = LS.sweep([A for A, _ in held], [b for _, b in held], bs=8, maxit=3000)
     plain, learned, best, fb = LS.evaluate(net, swh)
 
     def solve(P, name):

@@ -90,7 +90,8 @@ typedef struct hbmc_options {
                            right-hand side, dinv and same-block runs staged by bulk copy when
                            bs is 4 or 8 -- else 1);
                            1 = one CUDA block per level-1 block(s);
-                           2 = TMA-fed persistent warp-specialized kernels (w = 32);
+                           2 = retired (TMA-fed persistent warp-specialized kernels, removed:
+                               bit-identical to the others and never faster); runs as 0;
                            3 = one warp per level-1 block reading its runs with plain loads,
                                and SpMV one warp per level-1 block too (w = 32);
                            4 = one CUDA block of loader threads per level-1 block for every
@@ -455,6 +456,11 @@ typedef struct hbmc_batch hbmc_batch; /* opaque */
  * opt->precision, loop_mode and device apply to the batch. */
 hbmc_status hbmc_batch_build(int32_t nsys, const hbmc_system *systems, int32_t bs,
                              const hbmc_options *opt, hbmc_batch **out);
+/* The same with w (Section 4.2's level-1 block width: w BMC blocks of a color
+ * per level-1 block, w rows per SELL slice) 16 or 32; with w = 16 a warp
+ * runs two level-1 blocks.  hbmc_batch_features needs w = 32. */
+hbmc_status hbmc_batch_build_w(int32_t nsys, const hbmc_system *systems, int32_t bs, int32_t w,
+                               const hbmc_options *opt, hbmc_batch **out);
 void hbmc_batch_destroy(hbmc_batch *b);
 const char *hbmc_batch_last_error(const hbmc_batch *b);
 
@@ -493,6 +499,14 @@ hbmc_status hbmc_batch_iccg(hbmc_batch *b, const double *b_dev, double *x_dev, d
 hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
                                 int32_t ncand, const hbmc_options *opt, const double *b_dev, double tol,
                                 int64_t maxit, const char *cache_path, int32_t *best_bs, double *ms);
+/* The same over every pair (bs_candidates[i], w_candidates[j]) (w 16 or 32;
+ * the SELL slice height is w): ms[i * nw + j] (may be NULL) receives the
+ * timed solve of that pair or -1; *best_bs, *best_w the fastest pair.  The
+ * cache key includes both candidate lists. */
+hbmc_status hbmc_batch_autotune_w(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
+                                  int32_t nbs, const int32_t *w_candidates, int32_t nw, const hbmc_options *opt,
+                                  const double *b_dev, double tol, int64_t maxit, const char *cache_path,
+                                  int32_t *best_bs, int32_t *best_w, double *ms);
 
 /* Per-system feature vectors of a batch (host float[nsys *
  * HBMC_NUM_FEATURES], same definitions as hbmc_features). */

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libhbmc.so")
 OBJDIR = os.path.join(PKG, "_build")
 
-SOURCES = ["build_host.cpp", "batch_host.cpp", "kernels.cu", "sweep_warp.cu", "sweep_tw.cu", "sweep_wide.cu", "sweep_dag.cu", "sweep_tma.cu", "spmv_tma.cu", "sor.cu", "bicgstab.cu", "persistent.cu", "api.cu",
+SOURCES = ["build_host.cpp", "batch_host.cpp", "kernels.cu", "sweep_warp.cu", "sweep_tw.cu", "sweep_wide.cu", "sweep_dag.cu", "spmv_tma.cu", "sor.cu", "bicgstab.cu", "persistent.cu", "api.cu",
            "noalloc.cu", "batch.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

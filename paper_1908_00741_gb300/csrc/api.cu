@@ -213,7 +213,9 @@ hbmc_status upload(hbmc_ctx *ctx) {
   CK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
   while ((1 << d.lw) < d.w) ++d.lw;
   hbmc::sweep_geometry(h, d, ctx->opt.sweep_tpb);
-  d.sweep_kernel = ctx->opt.sweep_kernel;
+  // 2 named TMA-fed persistent warp-specialized kernels, since retired
+  // (bit-identical to the others and never faster); it runs as 0
+  d.sweep_kernel = ctx->opt.sweep_kernel == 2 ? 0 : ctx->opt.sweep_kernel;
   d.rec_ints = h.rec_ints;
   if (h.ntiles > 0) {
     TRY(dupload(ctx, d.rec_f, h.rec_f));
@@ -254,14 +256,6 @@ hbmc_status upload(hbmc_ctx *ctx) {
   CK(hbmc::setup_persistent());
   if (h.nc > 0) TRY(dupload(ctx, d.tile_ptr_dev, h.tile_ptr));
   TRY(dalloc(ctx, d.pbar, 4));
-  if (d.sweep_kernel == 2) {
-    std::vector<int32_t> rf, rb;
-    hbmc::plan_tma(h, d.tma_f, d.tma_b, rf, rb);
-    if (!rf.empty()) TRY(dupload(ctx, d.tma_f.rec, rf));
-    if (!rb.empty()) TRY(dupload(ctx, d.tma_b.rec, rb));
-    d.use_tma = 1;
-    CK(hbmc::setup_tma_kernels(d));
-  }
   d.part_len = hbmc::partials_needed(d);
   TRY(dalloc(ctx, d.part, (size_t)d.part_len));
   TRY(dalloc(ctx, d.hist, (size_t)hbmc::kHistCap));

@@ -77,8 +77,27 @@ __global__ void k_bgather_out(const double *src, const int32_t *__restrict__ pi,
 }
 
 // ---------------------------------------------------------------------------
-// SpMV-shaped kernels, one warp per level-1 block
+// SpMV-shaped kernels, W lanes per level-1 block (w = W): a warp holds 32 / W
+// level-1 blocks.  Work is predicated, not skipped by early returns, so that
+// every lane reaches the per-level-1-block reductions.
 // ---------------------------------------------------------------------------
+template <int W>
+struct Lanes {
+  static constexpr int kPerWarp = 32 / W;
+  int sub, j;  // level-1 block within the warp, lane within the level-1 block
+  unsigned mask;
+  __device__ Lanes(int lane)
+      : sub(lane / W), j(lane % W), mask(W == 32 ? 0xffffffffu : (0xffffu << (16 * (lane / W)))) {}
+};
+
+// sum over the W lanes of a level-1 block (every lane of the warp calls it)
+template <int W>
+__device__ __forceinline__ double unit_sum(double v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 struct ARun {
   const int32_t *rec;
   int rec_ints;
@@ -86,45 +105,53 @@ struct ARun {
   const double *val;
   int bs;
   int64_t units;
-  uint32_t off_t, warp_bytes;
+  uint32_t off_t, unit_bytes;
 };
 
-__device__ __forceinline__ double *spmv_unit(const ARun &a, unsigned char *smem, int warp, int lane, int64_t u,
-                                             const double *x) {
-  unsigned char *ws = smem + (size_t)warp * a.warp_bytes;
+template <int W>
+__device__ __forceinline__ int64_t unit_of(int warp, const Lanes<W> &ln) {
+  return ((int64_t)blockIdx.x * kBWpb + warp) * Lanes<W>::kPerWarp + ln.sub;
+}
+
+template <int W>
+__device__ __forceinline__ double *spmv_unit(const ARun &a, unsigned char *smem, int warp, const Lanes<W> &ln,
+                                             int64_t u, const double *x) {
+  unsigned char *ws = smem + (size_t)(warp * Lanes<W>::kPerWarp + ln.sub) * a.unit_bytes;
   int32_t *rs = reinterpret_cast<int32_t *>(ws);
   double *ts = reinterpret_cast<double *>(ws + a.off_t);
   const int32_t *rc = a.rec + u * a.rec_ints;
-  for (int k = lane; k < a.rec_ints; k += 32) rs[k] = rc[k];
-  for (int l = 0; l < a.bs; ++l) ts[(l << 5) + lane] = 0.0;
-  __syncwarp();
-  run_accumulate<double, double, false>(a.col, a.val, x, rec64(rs, 2), rs[0], rs + 6, ts, lane);
+  for (int k = ln.j; k < a.rec_ints; k += W) rs[k] = rc[k];
+  for (int l = 0; l < a.bs; ++l) ts[l * W + ln.j] = 0.0;
+  __syncwarp(ln.mask);
+  run_accumulate<double, double, false, W>(a.col, a.val, x, rec64(rs, 2), rs[0], rs + 6, ts, ln.j);
   return ts;
 }
 
 // mode 0: r = b - A x with ||b||^2 -> part0, ||r||^2 -> part1 (every system);
 // mode 1: ||b - A x||^2 -> part0 (true residual after the loop).
-template <int kMode>
+template <int kMode, int W>
 __global__ void __launch_bounds__(32 * kBWpb)
     k_bresid_w(const ARun a, const double *b, const double *x, double *r, double *part0, double *part1) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u = (int64_t)blockIdx.x * kBWpb + warp;
-  if (u >= a.units) return;
-  const double *ts = spmv_unit(a, smem, warp, lane, u, x);
-  const int64_t row0 = u * (int64_t)a.bs * 32;
+  const int warp = threadIdx.x >> 5;
+  const Lanes<W> ln(threadIdx.x & 31);
+  const int64_t u = unit_of<W>(warp, ln);
   double bb = 0.0, rr = 0.0;
-  for (int l = 0; l < a.bs; ++l) {
-    const int64_t row = row0 + (l << 5) + lane;
-    const double bi = b[row];
-    const double ri = bi - ts[(l << 5) + lane];
-    if (kMode == 0) r[row] = ri;
-    bb = fma(bi, bi, bb);
-    rr = fma(ri, ri, rr);
+  if (u < a.units) {
+    const double *ts = spmv_unit<W>(a, smem, warp, ln, u, x);
+    const int64_t row0 = u * (int64_t)a.bs * W;
+    for (int l = 0; l < a.bs; ++l) {
+      const int64_t row = row0 + l * W + ln.j;
+      const double bi = b[row];
+      const double ri = bi - ts[l * W + ln.j];
+      if (kMode == 0) r[row] = ri;
+      bb = fma(bi, bi, bb);
+      rr = fma(ri, ri, rr);
+    }
   }
-  bb = warp_sum(bb);
-  rr = warp_sum(rr);
-  if (lane == 0) {
+  bb = unit_sum<W>(bb);
+  rr = unit_sum<W>(rr);
+  if (u < a.units && ln.j == 0) {
     if (kMode == 0) {
       part0[u] = bb;
       part1[u] = rr;
@@ -134,69 +161,70 @@ __global__ void __launch_bounds__(32 * kBWpb)
   }
 }
 
+template <int W>
 __global__ void __launch_bounds__(32 * kBWpb)
     k_bspmv_w(const ARun a, const int32_t *__restrict__ unit_sys, const BSys *bsys, const double *p, double *q,
               double *part0) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u = (int64_t)blockIdx.x * kBWpb + warp;
-  if (u >= a.units) return;
-  if (sys_done(bsys, unit_sys, u)) {
-    if (lane == 0) part0[u] = 0.0;
-    return;
-  }
-  const double *ts = spmv_unit(a, smem, warp, lane, u, p);
-  const int64_t row0 = u * (int64_t)a.bs * 32;
+  const int warp = threadIdx.x >> 5;
+  const Lanes<W> ln(threadIdx.x & 31);
+  const int64_t u = unit_of<W>(warp, ln);
+  const bool live = u < a.units && !sys_done(bsys, unit_sys, u);
   double pq = 0.0;
-  for (int l = 0; l < a.bs; ++l) {
-    const int64_t row = row0 + (l << 5) + lane;
-    const double qv = ts[(l << 5) + lane];
-    q[row] = qv;
-    pq = fma(p[row], qv, pq);
+  if (live) {
+    const double *ts = spmv_unit<W>(a, smem, warp, ln, u, p);
+    const int64_t row0 = u * (int64_t)a.bs * W;
+    for (int l = 0; l < a.bs; ++l) {
+      const int64_t row = row0 + l * W + ln.j;
+      const double qv = ts[l * W + ln.j];
+      q[row] = qv;
+      pq = fma(p[row], qv, pq);
+    }
   }
-  pq = warp_sum(pq);
-  if (lane == 0) part0[u] = pq;
+  pq = unit_sum<W>(pq);
+  if (u < a.units && ln.j == 0) part0[u] = live ? pq : 0.0;
 }
 
 // x += alpha_s p, r -= alpha_s q, ||r||^2 partial
+template <int W>
 __global__ void __launch_bounds__(32 * kBWpb)
     k_bupdate_xr_w(int bs, int64_t units, const int32_t *__restrict__ unit_sys, const BSys *bsys, const double *p,
                    const double *q, double *x, double *r, double *part0) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u = (int64_t)blockIdx.x * kBWpb + warp;
-  if (u >= units) return;
-  const BSys &s = bsys[unit_sys[u]];
-  if (s.done) {
-    if (lane == 0) part0[u] = 0.0;
-    return;
-  }
-  const double alpha = s.alpha;
-  const int64_t row0 = u * (int64_t)bs * 32;
+  const int warp = threadIdx.x >> 5;
+  const Lanes<W> ln(threadIdx.x & 31);
+  const int64_t u = unit_of<W>(warp, ln);
+  const bool live = u < units && !sys_done(bsys, unit_sys, u);
   double rr = 0.0;
-  for (int l = 0; l < bs; ++l) {
-    const int64_t row = row0 + (l << 5) + lane;
-    x[row] = fma(alpha, p[row], x[row]);
-    const double ri = fma(-alpha, q[row], r[row]);
-    r[row] = ri;
-    rr = fma(ri, ri, rr);
+  if (live) {
+    const double alpha = bsys[unit_sys[u]].alpha;
+    const int64_t row0 = u * (int64_t)bs * W;
+    for (int l = 0; l < bs; ++l) {
+      const int64_t row = row0 + l * W + ln.j;
+      x[row] = fma(alpha, p[row], x[row]);
+      const double ri = fma(-alpha, q[row], r[row]);
+      r[row] = ri;
+      rr = fma(ri, ri, rr);
+    }
   }
-  rr = warp_sum(rr);
-  if (lane == 0) part0[u] = rr;
+  rr = unit_sum<W>(rr);
+  if (u < units && ln.j == 0) part0[u] = live ? rr : 0.0;
 }
 
 // p = z (mode 0) or p = z + beta_s p (mode 1)
+template <int W>
 __global__ void __launch_bounds__(32 * kBWpb)
     k_bupdate_p_w(int bs, int64_t units, const int32_t *__restrict__ unit_sys, const BSys *bsys, const double *z,
                   double *p, int mode) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u = (int64_t)blockIdx.x * kBWpb + warp;
-  if (u >= units) return;
+  const int warp = threadIdx.x >> 5;
+  const Lanes<W> ln(threadIdx.x & 31);
+  const int64_t u = unit_of<W>(warp, ln);
+  if (u >= units) return;  // no reduction follows
   const BSys &s = bsys[unit_sys[u]];
   if (s.done) return;
   const double beta = s.beta;
-  const int64_t row0 = u * (int64_t)bs * 32;
+  const int64_t row0 = u * (int64_t)bs * W;
   for (int l = 0; l < bs; ++l) {
-    const int64_t row = row0 + (l << 5) + lane;
+    const int64_t row = row0 + l * W + ln.j;
     p[row] = mode == 0 ? z[row] : fma(beta, p[row], z[row]);
   }
 }
@@ -214,95 +242,96 @@ struct BSweep {
   const T *dinv;
   int bs, rec_ints;
   int64_t tile0, ntiles;
-  uint32_t off_t, off_d, off_iv, off_im, warp_bytes;
+  uint32_t off_t, off_d, off_iv, off_im, unit_bytes;
 };
 
-template <typename T, typename IN>
-__device__ __forceinline__ T *stage(const BSweep<T> &a, unsigned char *smem, int warp, int lane, int64_t u,
-                                    const IN *in, int32_t *&rs, T *&ds, T *&iv, uint8_t *&im) {
-  unsigned char *ws = smem + (size_t)warp * a.warp_bytes;
+template <typename T, typename IN, int W>
+__device__ __forceinline__ T *stage(const BSweep<T> &a, unsigned char *smem, int warp, const Lanes<W> &ln,
+                                    int64_t u, const IN *in, int32_t *&rs, T *&ds, T *&iv, uint8_t *&im) {
+  unsigned char *ws = smem + (size_t)(warp * Lanes<W>::kPerWarp + ln.sub) * a.unit_bytes;
   rs = reinterpret_cast<int32_t *>(ws);
   T *ts = reinterpret_cast<T *>(ws + a.off_t);
   ds = reinterpret_cast<T *>(ws + a.off_d);
   iv = reinterpret_cast<T *>(ws + a.off_iv);
   im = ws + a.off_im;
   const int32_t *rc = a.rec + u * a.rec_ints;
-  for (int k = lane; k < a.rec_ints; k += 32) rs[k] = rc[k];
-  const int64_t row0 = u * (int64_t)a.bs * 32;
+  for (int k = ln.j; k < a.rec_ints; k += W) rs[k] = rc[k];
+  const int64_t row0 = u * (int64_t)a.bs * W;
   for (int l = 0; l < a.bs; ++l) {
-    const int64_t row = row0 + (l << 5) + lane;
-    ts[(l << 5) + lane] = (T)in[row];
-    ds[(l << 5) + lane] = a.dinv[row];
+    const int64_t row = row0 + l * W + ln.j;
+    ts[l * W + ln.j] = (T)in[row];
+    ds[l * W + ln.j] = a.dinv[row];
   }
-  __syncwarp();
+  __syncwarp(ln.mask);
   const int ilen = rs[1];
   const int64_t ibeg = rec64(rs, 4);
-  for (int e = lane; e < ilen; e += 32) {
+  for (int e = ln.j; e < ilen; e += W) {
     iv[e] = a.i_val[ibeg + e];
     im[e] = a.i_m[ibeg + e];
   }
+  __syncwarp(ln.mask);
   return ts;
 }
 
-template <typename T, typename Y>
+template <typename T, typename Y, int W>
 __global__ void __launch_bounds__(32 * kBWpb)
     k_bfwd_w(const BSweep<T> a, const int32_t *__restrict__ unit_sys, const BSys *bsys, const double *__restrict__ r,
              Y *y) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u = a.tile0 + (int64_t)blockIdx.x * kBWpb + warp;
-  if (u >= a.tile0 + a.ntiles || sys_done(bsys, unit_sys, u)) return;
+  const int warp = threadIdx.x >> 5;
+  const Lanes<W> ln(threadIdx.x & 31);
+  const int64_t u = a.tile0 + unit_of<W>(warp, ln);
+  if (u >= a.tile0 + a.ntiles || sys_done(bsys, unit_sys, u)) return;  // no reduction follows
   int32_t *rs;
   T *ds, *iv;
   uint8_t *im;
-  T *ts = stage<T, double>(a, smem, warp, lane, u, r, rs, ds, iv, im);
-  run_accumulate<T, Y, true>(a.o_col, a.o_val, y, rec64(rs, 2), rs[0], rs + 6, ts, lane);
+  T *ts = stage<T, double, W>(a, smem, warp, ln, u, r, rs, ds, iv, im);
+  run_accumulate<T, Y, true, W>(a.o_col, a.o_val, y, rec64(rs, 2), rs[0], rs + 6, ts, ln.j);
   const int32_t *i_rel = rs + 7 + a.bs;
   for (int l = 0; l < a.bs; ++l) {
-    T acc = ts[(l << 5) + lane];
+    T acc = ts[l * W + ln.j];
     const int pe = i_rel[l + 1];
-    for (int p = i_rel[l] + lane; p < pe; p += 32) acc = fma(-iv[p], ts[(im[p] << 5) + lane], acc);
-    ts[(l << 5) + lane] = acc * ds[(l << 5) + lane];
+    for (int p = i_rel[l] + ln.j; p < pe; p += W) acc = fma(-iv[p], ts[im[p] * W + ln.j], acc);
+    ts[l * W + ln.j] = acc * ds[l * W + ln.j];
   }
-  Y *yo = y + u * (int64_t)a.bs * 32;
-  for (int l = 0; l < a.bs; ++l) yo[(l << 5) + lane] = (Y)ts[(l << 5) + lane];
+  Y *yo = y + u * (int64_t)a.bs * W;
+  for (int l = 0; l < a.bs; ++l) yo[l * W + ln.j] = (Y)ts[l * W + ln.j];
 }
 
-template <typename T, typename Y>
+template <typename T, typename Y, int W>
 __global__ void __launch_bounds__(32 * kBWpb)
     k_bbwd_w(const BSweep<T> a, const int32_t *__restrict__ unit_sys, const BSys *bsys, const Y *__restrict__ yin,
              double *z, const double *__restrict__ r, int dot, double *part0) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u = a.tile0 + (int64_t)blockIdx.x * kBWpb + warp;
-  if (u >= a.tile0 + a.ntiles) return;
-  if (sys_done(bsys, unit_sys, u)) {
-    if (dot && lane == 0) part0[u] = 0.0;
-    return;
-  }
-  int32_t *rs;
-  T *ds, *iv;
-  uint8_t *im;
-  T *ts = stage<T, Y>(a, smem, warp, lane, u, yin, rs, ds, iv, im);
-  run_accumulate<T, double, true>(a.o_col, a.o_val, z, rec64(rs, 2), rs[0], rs + 6, ts, lane);
-  const int32_t *i_rel = rs + 7 + a.bs;
-  for (int l = a.bs - 1; l >= 0; --l) {
-    T acc = ts[(l << 5) + lane];
-    const int pe = i_rel[l + 1];
-    for (int p = i_rel[l] + lane; p < pe; p += 32) acc = fma(-iv[p], ts[(im[p] << 5) + lane], acc);
-    ts[(l << 5) + lane] = acc * ds[(l << 5) + lane];
-  }
-  const int64_t row0 = u * (int64_t)a.bs * 32;
+  const int warp = threadIdx.x >> 5;
+  const Lanes<W> ln(threadIdx.x & 31);
+  const int64_t u = a.tile0 + unit_of<W>(warp, ln);
+  const bool in_range = u < a.tile0 + a.ntiles;
+  const bool live = in_range && !sys_done(bsys, unit_sys, u);
   double rz = 0.0;
-  for (int l = 0; l < a.bs; ++l) {
-    const double zv = (double)ts[(l << 5) + lane];
-    z[row0 + (l << 5) + lane] = zv;
-    if (dot) rz = fma(r[row0 + (l << 5) + lane], zv, rz);
+  if (live) {
+    int32_t *rs;
+    T *ds, *iv;
+    uint8_t *im;
+    T *ts = stage<T, Y, W>(a, smem, warp, ln, u, yin, rs, ds, iv, im);
+    run_accumulate<T, double, true, W>(a.o_col, a.o_val, z, rec64(rs, 2), rs[0], rs + 6, ts, ln.j);
+    const int32_t *i_rel = rs + 7 + a.bs;
+    for (int l = a.bs - 1; l >= 0; --l) {
+      T acc = ts[l * W + ln.j];
+      const int pe = i_rel[l + 1];
+      for (int p = i_rel[l] + ln.j; p < pe; p += W) acc = fma(-iv[p], ts[im[p] * W + ln.j], acc);
+      ts[l * W + ln.j] = acc * ds[l * W + ln.j];
+    }
+    const int64_t row0 = u * (int64_t)a.bs * W;
+    for (int l = 0; l < a.bs; ++l) {
+      const double zv = (double)ts[l * W + ln.j];
+      z[row0 + l * W + ln.j] = zv;
+      if (dot) rz = fma(r[row0 + l * W + ln.j], zv, rz);
+    }
   }
-  if (dot) {
-    rz = warp_sum(rz);
-    if (lane == 0) part0[u] = rz;
-  }
+  if (!dot) return;  // uniform over the launch
+  rz = unit_sum<W>(rz);
+  if (in_range && ln.j == 0) part0[u] = live ? rz : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -386,17 +415,18 @@ __global__ void __launch_bounds__(kFinishThreads)
 __global__ void __launch_bounds__(128)
     k_bic0(const int64_t *__restrict__ lrp, const int32_t *__restrict__ lci, const double *__restrict__ laval,
            const double *__restrict__ adiag, const double *__restrict__ scale, const int32_t *__restrict__ unit_sys,
-           double *lval, double *ldiag, double *dinv, int bs, int64_t tile0, int64_t ntiles, long long *bad) {
+           double *lval, double *ldiag, double *dinv, int bs, int w, int64_t tile0, int64_t ntiles,
+           long long *bad) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t tl = g >> 5;
+  const int64_t tl = g / w;
   if (tl >= ntiles) return;
-  const int j = (int)(g & 31);
+  const int j = (int)(g % w);
   const int64_t u = tile0 + tl;
   const int32_t s = unit_sys[u];
   if (bad[s] != LLONG_MAX) return;  // this system failed in an earlier color
   const double sc = scale[s];
   for (int l = 0; l < bs; ++l) {
-    const int64_t i = (u * bs + l) * 32 + j;
+    const int64_t i = (u * bs + l) * w + j;
     const int64_t e0 = lrp[i], e1 = lrp[i + 1];
     for (int64_t e = e0; e < e1; ++e) {
       const int64_t jj = lci[e];
@@ -526,7 +556,7 @@ hbmc::ARun arun(const DeviceLayout &d) {
   a.bs = d.bs;
   a.units = d.tile_ptr[d.nc];
   a.off_t = d.wp_spmv.off_t;
-  a.warp_bytes = d.wp_spmv.warp_bytes;
+  a.unit_bytes = d.wp_spmv.warp_bytes;
   return a;
 }
 
@@ -554,39 +584,53 @@ hbmc::BSweep<T> bsweep(const DeviceLayout &d, bool fwd, int c) {
   a.off_d = w.off_d;
   a.off_iv = w.off_iv;
   a.off_im = w.off_im;
-  a.warp_bytes = w.warp_bytes;
+  a.unit_bytes = w.warp_bytes;
   return a;
 }
 
+// level-1 blocks per warp and per CUDA block of the batched kernels
+int per_warp(const DeviceLayout &d) { return 32 / d.w; }
+int64_t per_block(const DeviceLayout &d) { return (int64_t)hbmc::kBWpb * per_warp(d); }
+
 size_t sweep_smem(const DeviceLayout &d, bool fwd, int prec) {
   const hbmc::WarpPlan &w = prec == HBMC_PREC_F64 ? (fwd ? d.wp_f64_f : d.wp_f64_b) : (fwd ? d.wp_f32_f : d.wp_f32_b);
-  return (size_t)hbmc::kBWpb * w.warp_bytes;
+  return (size_t)per_block(d) * w.warp_bytes;
 }
 
-void enq_fwd(hbmc_batch *b, const View &v, int prec, cudaStream_t s) {
-  const DeviceLayout &d = *v.d;
+template <int W>
+void enq_fwd_w(hbmc_batch *b, const DeviceLayout &d, int prec, cudaStream_t s) {
   for (int c = 0; c < d.nc; ++c) {
-    const unsigned grid = hbmc::nblk(d.tile_ptr[c + 1] - d.tile_ptr[c], hbmc::kBWpb);
+    const unsigned grid = hbmc::nblk(d.tile_ptr[c + 1] - d.tile_ptr[c], (int)per_block(d));
     if (prec == HBMC_PREC_F64)
-      hbmc::k_bfwd_w<double, double><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, true, prec), s>>>(
+      hbmc::k_bfwd_w<double, double, W><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, true, prec), s>>>(
           bsweep<double>(d, true, c), b->unit_sys, b->bsys, d.r, d.y);
     else
-      hbmc::k_bfwd_w<float, float><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, true, prec), s>>>(
+      hbmc::k_bfwd_w<float, float, W><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, true, prec), s>>>(
           bsweep<float>(d, true, c), b->unit_sys, b->bsys, d.r, d.y32);
   }
 }
 
-void enq_bwd(hbmc_batch *b, const View &v, int prec, int dot, cudaStream_t s) {
-  const DeviceLayout &d = *v.d;
+template <int W>
+void enq_bwd_w(hbmc_batch *b, const DeviceLayout &d, int prec, int dot, cudaStream_t s) {
   for (int c = d.nc - 1; c >= 0; --c) {
-    const unsigned grid = hbmc::nblk(d.tile_ptr[c + 1] - d.tile_ptr[c], hbmc::kBWpb);
+    const unsigned grid = hbmc::nblk(d.tile_ptr[c + 1] - d.tile_ptr[c], (int)per_block(d));
     if (prec == HBMC_PREC_F64)
-      hbmc::k_bbwd_w<double, double><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, false, prec), s>>>(
+      hbmc::k_bbwd_w<double, double, W><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, false, prec), s>>>(
           bsweep<double>(d, false, c), b->unit_sys, b->bsys, d.y, d.z, d.r, dot, b->part0);
     else
-      hbmc::k_bbwd_w<float, float><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, false, prec), s>>>(
+      hbmc::k_bbwd_w<float, float, W><<<grid, 32 * hbmc::kBWpb, sweep_smem(d, false, prec), s>>>(
           bsweep<float>(d, false, c), b->unit_sys, b->bsys, d.y32, d.z, d.r, dot, b->part0);
   }
+}
+
+void enq_fwd(hbmc_batch *b, const View &v, int prec, cudaStream_t s) {
+  if (v.d->w == 16) enq_fwd_w<16>(b, *v.d, prec, s);
+  else enq_fwd_w<32>(b, *v.d, prec, s);
+}
+
+void enq_bwd(hbmc_batch *b, const View &v, int prec, int dot, cudaStream_t s) {
+  if (v.d->w == 16) enq_bwd_w<16>(b, *v.d, prec, dot, s);
+  else enq_bwd_w<32>(b, *v.d, prec, dot, s);
 }
 
 template <int kMode>
@@ -595,46 +639,65 @@ void enq_finish(hbmc_batch *b, cudaStream_t s, int use_cond, cudaGraphConditiona
       b->meta.nsys, b->meta.nc, b->cu_start, b->cu_count, b->part0, b->part1, b->bsys, b->bg, use_cond, h);
 }
 
-void enq_init(hbmc_batch *b, const View &v, int prec, cudaStream_t s) {
+template <int W>
+void enq_init_w(hbmc_batch *b, const View &v, int prec, cudaStream_t s) {
   const DeviceLayout &d = *v.d;
   const hbmc::ARun a = arun(d);
-  const unsigned ug = hbmc::nblk(a.units, hbmc::kBWpb);
-  const size_t sm = (size_t)hbmc::kBWpb * a.warp_bytes;
+  const unsigned ug = hbmc::nblk(a.units, (int)per_block(d));
+  const size_t sm = (size_t)per_block(d) * a.unit_bytes;
   hbmc::k_bgather_in<<<hbmc::nblk(d.n_pad, 256), 256, 0, s>>>(d.b, d.inv, d.n_pad, b->bg, 0);
   hbmc::k_bgather_in<<<hbmc::nblk(d.n_pad, 256), 256, 0, s>>>(d.x, d.inv, d.n_pad, b->bg, 1);
-  hbmc::k_bresid_w<0><<<ug, 32 * hbmc::kBWpb, sm, s>>>(a, d.b, d.x, d.r, b->part0, b->part1);
+  hbmc::k_bresid_w<0, W><<<ug, 32 * hbmc::kBWpb, sm, s>>>(a, d.b, d.x, d.r, b->part0, b->part1);
   enq_finish<hbmc::F_INIT>(b, s, 0, 0);
   enq_fwd(b, v, prec, s);
   enq_bwd(b, v, prec, 1, s);
   enq_finish<hbmc::F_RZ_INIT>(b, s, 0, 0);
-  hbmc::k_bupdate_p_w<<<ug, 32 * hbmc::kBWpb, 0, s>>>(d.bs, a.units, b->unit_sys, b->bsys, d.z, d.p, 0);
+  hbmc::k_bupdate_p_w<W><<<ug, 32 * hbmc::kBWpb, 0, s>>>(d.bs, a.units, b->unit_sys, b->bsys, d.z, d.p, 0);
 }
 
-void enq_body(hbmc_batch *b, const View &v, int prec, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h) {
+template <int W>
+void enq_body_w(hbmc_batch *b, const View &v, int prec, cudaStream_t s, int use_cond,
+                cudaGraphConditionalHandle h) {
   const DeviceLayout &d = *v.d;
   const hbmc::ARun a = arun(d);
-  const unsigned ug = hbmc::nblk(a.units, hbmc::kBWpb);
-  const size_t sm = (size_t)hbmc::kBWpb * a.warp_bytes;
-  hbmc::k_bspmv_w<<<ug, 32 * hbmc::kBWpb, sm, s>>>(a, b->unit_sys, b->bsys, d.p, d.q, b->part0);
+  const unsigned ug = hbmc::nblk(a.units, (int)per_block(d));
+  const size_t sm = (size_t)per_block(d) * a.unit_bytes;
+  hbmc::k_bspmv_w<W><<<ug, 32 * hbmc::kBWpb, sm, s>>>(a, b->unit_sys, b->bsys, d.p, d.q, b->part0);
   enq_finish<hbmc::F_PQ>(b, s, use_cond, h);
-  hbmc::k_bupdate_xr_w<<<ug, 32 * hbmc::kBWpb, 0, s>>>(d.bs, a.units, b->unit_sys, b->bsys, d.p, d.q, d.x, d.r,
-                                                        b->part0);
+  hbmc::k_bupdate_xr_w<W><<<ug, 32 * hbmc::kBWpb, 0, s>>>(d.bs, a.units, b->unit_sys, b->bsys, d.p, d.q, d.x, d.r,
+                                                           b->part0);
   enq_finish<hbmc::F_RR>(b, s, use_cond, h);
   enq_fwd(b, v, prec, s);
   enq_bwd(b, v, prec, 1, s);
   enq_finish<hbmc::F_RZ>(b, s, use_cond, h);
-  hbmc::k_bupdate_p_w<<<ug, 32 * hbmc::kBWpb, 0, s>>>(d.bs, a.units, b->unit_sys, b->bsys, d.z, d.p, 1);
+  hbmc::k_bupdate_p_w<W><<<ug, 32 * hbmc::kBWpb, 0, s>>>(d.bs, a.units, b->unit_sys, b->bsys, d.z, d.p, 1);
+}
+
+template <int W>
+void enq_final_w(hbmc_batch *b, const View &v, cudaStream_t s) {
+  const DeviceLayout &d = *v.d;
+  const hbmc::ARun a = arun(d);
+  const unsigned ug = hbmc::nblk(a.units, (int)per_block(d));
+  const size_t sm = (size_t)per_block(d) * a.unit_bytes;
+  hbmc::k_bgather_out<<<hbmc::nblk(d.n, 256), 256, 0, s>>>(d.x, d.pi, d.n, b->unit_sys, (int64_t)d.bs * d.w,
+                                                           b->bsys, b->bg);
+  hbmc::k_bresid_w<1, W><<<ug, 32 * hbmc::kBWpb, sm, s>>>(a, d.b, d.x, d.t, b->part0, nullptr);
+  enq_finish<hbmc::F_TRUE>(b, s, 0, 0);
+}
+
+void enq_init(hbmc_batch *b, const View &v, int prec, cudaStream_t s) {
+  if (v.d->w == 16) enq_init_w<16>(b, v, prec, s);
+  else enq_init_w<32>(b, v, prec, s);
+}
+
+void enq_body(hbmc_batch *b, const View &v, int prec, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h) {
+  if (v.d->w == 16) enq_body_w<16>(b, v, prec, s, use_cond, h);
+  else enq_body_w<32>(b, v, prec, s, use_cond, h);
 }
 
 void enq_final(hbmc_batch *b, const View &v, cudaStream_t s) {
-  const DeviceLayout &d = *v.d;
-  const hbmc::ARun a = arun(d);
-  const unsigned ug = hbmc::nblk(a.units, hbmc::kBWpb);
-  const size_t sm = (size_t)hbmc::kBWpb * a.warp_bytes;
-  hbmc::k_bgather_out<<<hbmc::nblk(d.n, 256), 256, 0, s>>>(d.x, d.pi, d.n, b->unit_sys, (int64_t)d.bs * 32,
-                                                           b->bsys, b->bg);
-  hbmc::k_bresid_w<1><<<ug, 32 * hbmc::kBWpb, sm, s>>>(a, d.b, d.x, d.t, b->part0, nullptr);
-  enq_finish<hbmc::F_TRUE>(b, s, 0, 0);
+  if (v.d->w == 16) enq_final_w<16>(b, v, s);
+  else enq_final_w<32>(b, v, s);
 }
 
 hbmc_status build_graph(hbmc_batch *b, const View &v, int prec) {
@@ -713,6 +776,17 @@ std::string fingerprint(int32_t nsys, const hbmc_system *sys) {
   return buf;
 }
 
+template <int W>
+void allow_batch(int cap) {
+  cudaFuncSetAttribute(hbmc::k_bfwd_w<double, double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(hbmc::k_bfwd_w<float, float, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(hbmc::k_bbwd_w<double, double, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(hbmc::k_bbwd_w<float, float, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(hbmc::k_bspmv_w<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(hbmc::k_bresid_w<0, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(hbmc::k_bresid_w<1, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
+
 }  // namespace
 
 extern "C" {
@@ -743,7 +817,13 @@ void hbmc_batch_destroy(hbmc_batch *b) {
 
 hbmc_status hbmc_batch_build(int32_t nsys, const hbmc_system *systems, int32_t bs, const hbmc_options *opt,
                              hbmc_batch **out) {
+  return hbmc_batch_build_w(nsys, systems, bs, 32, opt, out);
+}
+
+hbmc_status hbmc_batch_build_w(int32_t nsys, const hbmc_system *systems, int32_t bs, int32_t w,
+                               const hbmc_options *opt, hbmc_batch **out) {
   if (!out) return berr(nullptr, HBMC_ERR_INVALID_ARG, "out is null");
+  if (w != 16 && w != 32) return berr(nullptr, HBMC_ERR_INVALID_ARG, "batch: w must be 16 or 32");
   *out = nullptr;
   hbmc_options o;
   hbmc_default_options(&o);
@@ -762,7 +842,7 @@ hbmc_status hbmc_batch_build(int32_t nsys, const hbmc_system *systems, int32_t b
   std::string e;
   hbmc_status st;
   try {
-    st = hbmc::build_batch_host(nsys, systems, bs, 32, o, g, b->meta, e);
+    st = hbmc::build_batch_host(nsys, systems, bs, w, o, g, b->meta, e);
   } catch (const std::bad_alloc &) {
     st = HBMC_ERR_OOM;
     e = "host allocation failed";
@@ -800,20 +880,15 @@ hbmc_status hbmc_batch_build(int32_t nsys, const hbmc_system *systems, int32_t b
     return fail(HBMC_ERR_CUDA);
   }
   size_t need = 0;
-  for (const hbmc::WarpPlan *w : {&v.d->wp_f64_f, &v.d->wp_f64_b, &v.d->wp_f32_f, &v.d->wp_f32_b, &v.d->wp_spmv})
-    need = std::max(need, (size_t)hbmc::kBWpb * w->warp_bytes);
+  for (const hbmc::WarpPlan *wp : {&v.d->wp_f64_f, &v.d->wp_f64_b, &v.d->wp_f32_f, &v.d->wp_f32_b, &v.d->wp_spmv})
+    need = std::max(need, (size_t)per_block(*v.d) * wp->warp_bytes);
   if (need > 200 * 1024) {
     b->err = "batch: a level-1 block's same-block run does not fit in shared memory";
     return fail(HBMC_ERR_INVALID_ARG);
   }
   const int cap = 200 * 1024;
-  cudaFuncSetAttribute(hbmc::k_bfwd_w<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(hbmc::k_bfwd_w<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(hbmc::k_bbwd_w<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(hbmc::k_bbwd_w<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(hbmc::k_bspmv_w, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(hbmc::k_bresid_w<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(hbmc::k_bresid_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  if (w == 16) allow_batch<16>(cap);
+  else allow_batch<32>(cap);
   if (cudaGetLastError() != cudaSuccess) {
     b->err = "batch: kernel attribute setup failed";
     return fail(HBMC_ERR_CUDA);
@@ -869,8 +944,9 @@ hbmc_status hbmc_batch_ic0(hbmc_batch *b, const double *shifts, int64_t *bad_row
   hbmc::k_fill_ll<<<hbmc::nblk(m.nsys, 256), 256, 0, s>>>(b->bad, m.nsys, LLONG_MAX);
   for (int c = 0; c < d.nc; ++c) {
     const int64_t t0 = d.tile_ptr[c], nt = d.tile_ptr[c + 1] - t0;
-    hbmc::k_bic0<<<hbmc::nblk(nt * 32, 128), 128, 0, s>>>(d.lrp, d.lci, d.laval, d.adiag, b->scale, b->unit_sys,
-                                                          d.lval, d.ldiag, d.dinv, d.bs, t0, nt, b->bad);
+    hbmc::k_bic0<<<hbmc::nblk(nt * d.w, 128), 128, 0, s>>>(d.lrp, d.lci, d.laval, d.adiag, b->scale,
+                                                            b->unit_sys, d.lval, d.ldiag, d.dinv, d.bs, d.w, t0, nt,
+                                                            b->bad);
   }
   hbmc::enqueue_scatter_factor(d, true, s);
   std::vector<long long> bad(m.nsys);
@@ -967,6 +1043,7 @@ hbmc_status hbmc_batch_features(hbmc_batch *b, float *feat) {
   if (!b || !feat) return berr(b, HBMC_ERR_INVALID_ARG, "null argument");
   View v;
   if (!view(b, v)) return berr(b, HBMC_ERR_INVALID_ARG, "batch has no device context");
+  if (v.d->w != 32) return berr(b, HBMC_ERR_INVALID_ARG, "batch features need a batch built with w = 32");
   const hbmc::BatchMeta &m = b->meta;
   int prev = -1;
   cudaGetDevice(&prev);
@@ -992,20 +1069,37 @@ hbmc_status hbmc_batch_features(hbmc_batch *b, float *feat) {
 hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
                                 int32_t ncand, const hbmc_options *opt, const double *b_dev, double tol,
                                 int64_t maxit, const char *cache_path, int32_t *best_bs, double *ms) {
-  if (!best_bs || !bs_candidates || ncand < 1 || !b_dev)
+  const int32_t w32 = 32;
+  int32_t best_w = 0;
+  return hbmc_batch_autotune_w(nsys, systems, bs_candidates, ncand, &w32, 1, opt, b_dev, tol, maxit, cache_path,
+                               best_bs, &best_w, ms);
+}
+
+hbmc_status hbmc_batch_autotune_w(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
+                                  int32_t nbs, const int32_t *w_candidates, int32_t nw, const hbmc_options *opt,
+                                  const double *b_dev, double tol, int64_t maxit, const char *cache_path,
+                                  int32_t *best_bs, int32_t *best_w, double *ms) {
+  if (!best_bs || !best_w || !bs_candidates || nbs < 1 || !w_candidates || nw < 1 || !b_dev)
     return berr(nullptr, HBMC_ERR_INVALID_ARG, "autotune: bad arguments");
-  const std::string key = fingerprint(nsys, systems);
+  for (int32_t k = 0; k < nw; ++k)
+    if (w_candidates[k] != 16 && w_candidates[k] != 32)
+      return berr(nullptr, HBMC_ERR_INVALID_ARG, "autotune: w candidates must be 16 or 32");
+  // the cache key covers the candidate sets as well as the systems
+  std::string key = fingerprint(nsys, systems);
+  for (int32_t k = 0; k < nbs; ++k) key += "b" + std::to_string(bs_candidates[k]);
+  for (int32_t k = 0; k < nw; ++k) key += "w" + std::to_string(w_candidates[k]);
   if (cache_path) {
     std::ifstream in(cache_path);
     std::string line;
     while (std::getline(in, line)) {
       std::istringstream ls(line);
       std::string k;
-      int32_t v = 0;
-      if ((ls >> k >> v) && k == key) {
-        *best_bs = v;
+      int32_t vb = 0, vw = 0;
+      if ((ls >> k >> vb >> vw) && k == key) {
+        *best_bs = vb;
+        *best_w = vw;
         if (ms)
-          for (int32_t c = 0; c < ncand; ++c) ms[c] = -1.0;
+          for (int32_t c = 0; c < nbs * nw; ++c) ms[c] = -1.0;
         return HBMC_OK;
       }
     }
@@ -1015,49 +1109,54 @@ hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const 
   if (opt) o = *opt;
   double best = 1e300;
   *best_bs = -1;
+  *best_w = -1;
   int64_t n_total = 0;
   for (int32_t s = 0; s < nsys; ++s) n_total += systems[s].n;
   double *x = nullptr;
   if (cudaMalloc(&x, sizeof(double) * (n_total ? n_total : 1)) != cudaSuccess)
     return berr(nullptr, HBMC_ERR_OOM, "autotune: no memory for x");
-  for (int32_t c = 0; c < ncand; ++c) {
-    if (ms) ms[c] = -1.0;
-    const int32_t bs = bs_candidates[c];
-    if (!box_for(bs, o.box)) continue;
-    hbmc_batch *b = nullptr;
-    if (hbmc_batch_build(nsys, systems, bs, &o, &b) != HBMC_OK) continue;
-    double t = -1.0;
-    if (hbmc_batch_ic0(b, nullptr, nullptr) == HBMC_OK) {
-      View v;
-      view(b, v);
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      bool ok = true;
-      for (int rep = 0; rep < 2 && ok; ++rep) {
-        cudaMemsetAsync(x, 0, sizeof(double) * n_total, v.s);
-        cudaEventRecord(e0, v.s);
-        ok = hbmc_batch_iccg(b, b_dev, x, tol, maxit, nullptr, nullptr, nullptr, nullptr, nullptr) == HBMC_OK;
-        cudaEventRecord(e1, v.s);
-        cudaEventSynchronize(e1);
+  for (int32_t cb = 0; cb < nbs; ++cb) {
+    for (int32_t cw = 0; cw < nw; ++cw) {
+      const int32_t c = cb * nw + cw;
+      if (ms) ms[c] = -1.0;
+      const int32_t bs = bs_candidates[cb], w = w_candidates[cw];
+      if (!box_for(bs, o.box)) continue;
+      hbmc_batch *b = nullptr;
+      if (hbmc_batch_build_w(nsys, systems, bs, w, &o, &b) != HBMC_OK) continue;
+      double t = -1.0;
+      if (hbmc_batch_ic0(b, nullptr, nullptr) == HBMC_OK) {
+        View v;
+        view(b, v);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+          cudaMemsetAsync(x, 0, sizeof(double) * n_total, v.s);
+          cudaEventRecord(e0, v.s);
+          ok = hbmc_batch_iccg(b, b_dev, x, tol, maxit, nullptr, nullptr, nullptr, nullptr, nullptr) == HBMC_OK;
+          cudaEventRecord(e1, v.s);
+          cudaEventSynchronize(e1);
+        }
+        float f = 0.f;
+        if (ok && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess) t = f;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
       }
-      float f = 0.f;
-      if (ok && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess) t = f;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-    }
-    hbmc_batch_destroy(b);
-    if (ms) ms[c] = t;
-    if (t > 0 && t < best) {
-      best = t;
-      *best_bs = bs;
+      hbmc_batch_destroy(b);
+      if (ms) ms[c] = t;
+      if (t > 0 && t < best) {
+        best = t;
+        *best_bs = bs;
+        *best_w = w;
+      }
     }
   }
   cudaFree(x);
   if (*best_bs < 0) return berr(nullptr, HBMC_ERR_INVALID_ARG, "autotune: no candidate solved the batch");
   if (cache_path) {
     std::ofstream outf(cache_path, std::ios::app);
-    outf << key << " " << *best_bs << "\n";
+    outf << key << " " << *best_bs << " " << *best_w << "\n";
   }
   return HBMC_OK;
 }

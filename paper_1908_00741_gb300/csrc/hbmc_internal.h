@@ -149,15 +149,6 @@ struct Scalars {
 enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_BREAKDOWN = 3 };
 enum { CNT_RES = 0, CNT_PQ = 1, CNT_RR = 2, CNT_RZ = 3, CNT_TRUE = 4, CNT_S = 5, CNT_W = 6, CNT_RHO = 7 };
 
-// Shared-memory stage layout of the TMA-fed substitution kernels (byte
-// offsets inside one stage) for one direction and one value type.
-struct TmaLayout {
-  uint32_t off_in = 0, off_dinv = 0, off_aux = 0, off_ocol = 0, off_oval = 0, off_ival = 0,
-           off_im = 0, stage_bytes = 0;
-  int stages = 0;       // 0: does not fit, use the plain kernels
-  int ctas_per_sm = 0;  // resident CUDA blocks per SM at this layout
-};
-
 // Shared memory of one warp in the warp-per-unit kernels (byte offsets), and
 // warps per CUDA block; wpb = 0 means the plan does not fit.
 struct WarpPlan {
@@ -203,13 +194,6 @@ struct SpmvPlan {
   int stages = 0, blocks_per_sm = 0;
 };
 
-struct TmaPlan {
-  int32_t *rec = nullptr;  // device: per level-1 block record
-  int rec_ints = 0;
-  int64_t max_o = 0, max_i = 0;
-  TmaLayout f64, f32;
-};
-
 struct DeviceLayout;
 bool ctx_view(hbmc_ctx *ctx, const DeviceLayout **d, cudaStream_t *stream, int *device, bool *factored,
               std::string **err);
@@ -227,9 +211,7 @@ struct DeviceLayout {
   // when it fits)
   int32_t sweep_tpb = 1;
   int32_t sm_count = 1;  // streaming multiprocessors of the device
-  int32_t sweep_kernel = 0;  // 0 warp per unit, 1 block per unit, 2 TMA-fed (see hbmc_options)
-  int32_t use_tma = 0;   // substitutions through the TMA-fed kernels when their plan fits
-  TmaPlan tma_f, tma_b;
+  int32_t sweep_kernel = 0;  // hbmc_options.sweep_kernel (2 mapped to 0)
   // warp-per-unit kernels: device records and shared-memory plans
   int32_t rec_ints = 0;
   int32_t *rec_f = nullptr, *rec_b = nullptr, *rec_a = nullptr;

@@ -597,7 +597,7 @@ int64_t partials_needed(const DeviceLayout &d) {
   int64_t sweep = 0;
   for (int c = 0; c < d.nc; ++c) sweep += (d.tile_ptr[c + 1] - d.tile_ptr[c] + d.sweep_tpb - 1) / d.sweep_tpb;
   const int64_t rows = 2 * (int64_t)row_grid(d);
-  return std::max(std::max(std::max(sweep, rows), tma_partials_needed(d)), std::max(std::max(warp_partials_needed(d), tw_partials_needed(d)), std::max(spmv_tma_partials_needed(d), d.nc > 0 ? d.tile_ptr[d.nc] : (int64_t)0))) + 64;
+  return std::max(std::max(sweep, rows), std::max(std::max(warp_partials_needed(d), tw_partials_needed(d)), std::max(spmv_tma_partials_needed(d), d.nc > 0 ? d.tile_ptr[d.nc] : (int64_t)0))) + 64;
 }
 
 namespace {
@@ -708,7 +708,6 @@ void enqueue_fwd(const DeviceLayout &d, int prec, const double *r, bool check_do
     return;
   }
   if (warp_usable(d, true, prec)) return enqueue_fwd_warp(d, prec, r, check_done, s);
-  if (tma_usable(d, true, prec)) return enqueue_fwd_tma(d, prec, r, check_done, s);
   const Scalars *sc = check_done ? d.sc : nullptr;
   for (int c = 0; c < d.nc; ++c) {
     if (prec == HBMC_PREC_F64) {
@@ -743,7 +742,6 @@ void enqueue_bwd(const DeviceLayout &d, int prec, const double *r, int dot_mode,
     return;
   }
   if (warp_usable(d, false, prec)) return enqueue_bwd_warp(d, prec, r, dot_mode, check_done, s);
-  if (tma_usable(d, false, prec)) return enqueue_bwd_tma(d, prec, r, dot_mode, check_done, s);
   Scalars *sc = check_done || dot_mode ? d.sc : nullptr;
   int64_t total = 0;
   for (int c = 0; c < d.nc; ++c) total += sweep_grid(d, c);

@@ -91,16 +91,6 @@ bool sor_usable(const DeviceLayout &d);
 void enqueue_sor(const DeviceLayout &d, double *x, const double *b, double omega, int64_t sweeps, bool symmetric,
                  cudaStream_t s);
 
-// TMA-fed substitution kernels (sweep_tma.cu)
-void plan_tma(const HostLayout &h, TmaPlan &pf, TmaPlan &pb, std::vector<int32_t> &rec_f,
-              std::vector<int32_t> &rec_b);
-cudaError_t setup_tma_kernels(DeviceLayout &d);
-bool tma_usable(const DeviceLayout &d, bool fwd, int prec);
-int64_t tma_partials_needed(const DeviceLayout &d);
-void enqueue_fwd_tma(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);
-void enqueue_bwd_tma(const DeviceLayout &d, int prec, const double *r, int dot_mode, bool check_done,
-                     cudaStream_t s);
-
 void enqueue_gather_in(const DeviceLayout &d, const double *src, double *dst, int which, cudaStream_t s);
 void enqueue_gather_out(const DeviceLayout &d, const double *src, double *dst, bool to_user, cudaStream_t s);
 void enqueue_widen(const float *src, double *dst, int64_t n, cudaStream_t s);

@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(32 * kMaxWpb)
 
 uint32_t al16(uint64_t v) { return (uint32_t)((v + 15) & ~uint64_t(15)); }
 
-WarpPlan plan_warp(int bs, int rec_ints, int64_t max_i, size_t tsize) {
+WarpPlan plan_warp(int bs, int lanes, int rec_ints, int64_t max_i, size_t tsize) {
   WarpPlan w;
-  const uint64_t R = (uint64_t)bs * 32;
+  const uint64_t R = (uint64_t)bs * lanes;
   w.off_t = al16((uint64_t)rec_ints * 4);
   w.off_d = al16(w.off_t + R * tsize);
   w.off_iv = al16(w.off_d + R * tsize);
@@ -245,13 +245,16 @@ const WarpPlan &plan_of(const DeviceLayout &d, bool fwd, int prec) {
 }  // namespace
 
 void plan_warp_kernels(const HostLayout &h, DeviceLayout &d) {
-  d.wp_f64_f = plan_warp(h.bs, h.rec_ints, h.max_i_f, 8);
-  d.wp_f64_b = plan_warp(h.bs, h.rec_ints, h.max_i_b, 8);
-  d.wp_f32_f = plan_warp(h.bs, h.rec_ints, h.max_i_f, 4);
-  d.wp_f32_b = plan_warp(h.bs, h.rec_ints, h.max_i_b, 4);
+  // sized for one level-1 block of bs * w rows (the batched solver's
+  // kernels also run w = 16, two level-1 blocks per warp)
+  const int lanes = h.w == 16 ? 16 : 32;
+  d.wp_f64_f = plan_warp(h.bs, lanes, h.rec_ints, h.max_i_f, 8);
+  d.wp_f64_b = plan_warp(h.bs, lanes, h.rec_ints, h.max_i_b, 8);
+  d.wp_f32_f = plan_warp(h.bs, lanes, h.rec_ints, h.max_i_f, 4);
+  d.wp_f32_b = plan_warp(h.bs, lanes, h.rec_ints, h.max_i_b, 4);
   WarpPlan s;
   s.off_t = al16((uint64_t)h.rec_ints * 4);
-  s.warp_bytes = al16(s.off_t + (uint64_t)h.bs * 32 * 8);
+  s.warp_bytes = al16(s.off_t + (uint64_t)h.bs * lanes * 8);
   s.wpb = (uint64_t)kMaxWpb * s.warp_bytes <= kWarpSmemBudget ? kMaxWpb : 1;
   d.wp_spmv = s;
 }

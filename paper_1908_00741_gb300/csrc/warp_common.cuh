@@ -35,18 +35,19 @@ __device__ __forceinline__ double block_sum_rt(double v) {
 
 // ts[l] += sign * sum of the unit's run entries of slice l: v * src[col],
 // entries taken in run order (the per-row order fixed by the layout).  The
-// loads of kChunk entries are issued together before any is used.
-template <typename T, typename G, bool kNeg>
+// loads of kChunk entries are issued together before any is used.  W lanes
+// per level-1 block (w = W); `lane` is the lane within the level-1 block.
+template <typename T, typename G, bool kNeg, int W = 32>
 __device__ __forceinline__ void run_accumulate(const int32_t *__restrict__ col, const T *__restrict__ val,
                                                const G *src, int64_t beg, int len, const int32_t *rel,
                                                T *ts, int lane) {
   int l = 0;
-  for (int t0 = 0; t0 < len; t0 += kChunk * 32) {
+  for (int t0 = 0; t0 < len; t0 += kChunk * W) {
     int32_t c[kChunk];
     T v[kChunk], g[kChunk];
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
-      const int t = t0 + k * 32;
+      const int t = t0 + k * W;
       if (t < len) {
         c[k] = col[beg + t + lane];
         v[k] = val[beg + t + lane];
@@ -54,15 +55,15 @@ __device__ __forceinline__ void run_accumulate(const int32_t *__restrict__ col, 
     }
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
-      const int t = t0 + k * 32;
+      const int t = t0 + k * W;
       if (t < len) g[k] = (T)src[c[k]];
     }
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
-      const int t = t0 + k * 32;
+      const int t = t0 + k * W;
       if (t < len) {
         while (t >= rel[l + 1]) ++l;
-        T *slot = ts + (l << 5) + lane;
+        T *slot = ts + l * W + lane;
         *slot = fma(kNeg ? -v[k] : v[k], g[k], *slot);
       }
     }

@@ -47,9 +47,9 @@ EXPORTED = [
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
     "hbmc_debug_stall", "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar", "hbmc_ilu0", "hbmc_get_factor_u", "hbmc_bicgstab",
-    "hbmc_batch_build", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
+    "hbmc_batch_build", "hbmc_batch_build_w", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
     "hbmc_batch_set_stream", "hbmc_batch_set_precision", "hbmc_batch_ic0", "hbmc_batch_iccg",
-    "hbmc_batch_autotune", "hbmc_batch_features",
+    "hbmc_batch_autotune", "hbmc_batch_autotune_w", "hbmc_batch_features",
     "hbmc_features", "hbmc_shift_grid", "hbmc_mlp_num_params", "hbmc_mlp_create", "hbmc_mlp_destroy",
     "hbmc_mlp_last_error", "hbmc_mlp_set_params", "hbmc_mlp_get_params", "hbmc_mlp_forward",
     "hbmc_mlp_gradient", "hbmc_mlp_train", "hbmc_predict_shift", "hbmc_ic0_auto",
@@ -132,6 +132,7 @@ def load():
             "hbmc_get_factor_u": (I32, [P, P]),
             "hbmc_bicgstab": (I32, [P, P, P, D, I64, P, P, P]),
             "hbmc_batch_build": (I32, [I32, P, I32, P, P]),
+            "hbmc_batch_build_w": (I32, [I32, P, I32, I32, P, P]),
             "hbmc_batch_destroy": (None, [P]),
             "hbmc_batch_last_error": (ctypes.c_char_p, [P]),
             "hbmc_batch_info": (I32, [P, P, P, P, P]),
@@ -140,6 +141,7 @@ def load():
             "hbmc_batch_ic0": (I32, [P, P, P]),
             "hbmc_batch_iccg": (I32, [P, P, P, D, I64, P, P, P, P, P]),
             "hbmc_batch_autotune": (I32, [I32, P, P, I32, P, P, D, I64, ctypes.c_char_p, P, P]),
+            "hbmc_batch_autotune_w": (I32, [I32, P, P, I32, P, I32, P, P, D, I64, ctypes.c_char_p, P, P, P]),
             "hbmc_batch_features": (I32, [P, P]),
             "hbmc_features": (I32, [P, P]),
             "hbmc_shift_grid": (D, [I32]),
@@ -545,15 +547,16 @@ class Batch:
         return {"n": n.value, "n_pad": npad.value, "nc": nc.value, "units": nu.value}
 
 
-def hbmc_batch_build(mats, bs, *, use_boxes=True, precision=PREC_F64, loop_mode=LOOP_GRAPH, device=-1,
+def hbmc_batch_build(mats, bs, *, w=32, use_boxes=True, precision=PREC_F64, loop_mode=LOOP_GRAPH, device=-1,
                      check_every=16) -> Batch:
-    """Batch of CSR systems (box blocking for grid matrices when use_boxes)."""
+    """Batch of CSR systems (box blocking for grid matrices when use_boxes);
+    w = 32 or 16 BMC blocks per level-1 block."""
     lib = load()
     arr, keep = _systems(mats, use_boxes)
     opt = _box_opts(bs, precision, loop_mode, device, check_every)
     h = ctypes.c_void_p()
-    s = lib.hbmc_batch_build(len(mats), ctypes.cast(arr, ctypes.c_void_p), int(bs), ctypes.byref(opt),
-                             ctypes.byref(h))
+    s = lib.hbmc_batch_build_w(len(mats), ctypes.cast(arr, ctypes.c_void_p), int(bs), int(w), ctypes.byref(opt),
+                               ctypes.byref(h))
     if s != OK:
         raise HbmcError(s, lib.hbmc_batch_last_error(None).decode())
     del keep
@@ -611,6 +614,28 @@ def hbmc_batch_autotune(mats, b, bs_candidates=(4, 8, 16, 32), *, use_boxes=True
         raise HbmcError(s, lib.hbmc_batch_last_error(None).decode())
     del keep
     return int(best.value), ms
+
+
+def hbmc_batch_autotune_w(mats, b, bs_candidates=(4, 8, 16, 32), w_candidates=(16, 32), *, use_boxes=True,
+                          precision=PREC_F32, tol=1e-8, maxit=10000, cache_path=None, device=-1):
+    """Pick the (bs, w) pair that solves the batch fastest; returns (best_bs,
+    best_w, ms[len(bs_candidates), len(w_candidates)])."""
+    lib = load()
+    arr, keep = _systems(mats, use_boxes)
+    opt = _box_opts(8, precision, LOOP_GRAPH, device)
+    cb = np.ascontiguousarray(bs_candidates, dtype=np.int32)
+    cw = np.ascontiguousarray(w_candidates, dtype=np.int32)
+    ms = np.zeros(len(cb) * len(cw))
+    best_bs, best_w = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    n_total = sum(int(A.n) for A in mats)
+    s = lib.hbmc_batch_autotune_w(len(mats), ctypes.cast(arr, ctypes.c_void_p), _np_ptr(cb), len(cb), _np_ptr(cw),
+                                  len(cw), ctypes.byref(opt), _dev_ptr(b, n_total, "b"), float(tol), int(maxit),
+                                  cache_path.encode() if cache_path else None, ctypes.byref(best_bs),
+                                  ctypes.byref(best_w), _np_ptr(ms))
+    if s != OK:
+        raise HbmcError(s, lib.hbmc_batch_last_error(None).decode())
+    del keep
+    return int(best_bs.value), int(best_w.value), ms.reshape(len(cb), len(cw))
 
 
 # --------------------------------------------------------------------------

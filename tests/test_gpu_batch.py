@@ -31,11 +31,15 @@ def _concat(items):
 
 
 @pytest.mark.parametrize("bs", [4, 8, 16])
+@pytest.mark.parametrize("w", [32, 16])
 @pytest.mark.parametrize("loop_mode", [H.LOOP_GRAPH, H.LOOP_HOST])
-def test_batch_fp64_matches_oracle_per_system(lib, orc, bs, loop_mode):
+def test_batch_fp64_matches_oracle_per_system(lib, orc, bs, w, loop_mode):
+    """Every system of the batch, with w = 32 or 16 BMC blocks per level-1
+    block (two level-1 blocks per warp at 16), takes its own oracle solve's
+    iteration count and iterates."""
     items = _small_batch()
     mats = [A for A, _, _ in items]
-    batch = H.hbmc_batch_build(mats, bs, loop_mode=loop_mode, check_every=3)
+    batch = H.hbmc_batch_build(mats, bs, w=w, loop_mode=loop_mode, check_every=3)
     st, bad = H.hbmc_batch_ic0(batch)
     assert st == H.OK and np.all(bad == -1)
     b = torch.tensor(_concat(items), device="cuda")
@@ -46,7 +50,7 @@ def test_batch_fp64_matches_oracle_per_system(lib, orc, bs, loop_mode):
     off = 0
     box = W.box_for_bs(bs)
     for k, (A, bk, _) in enumerate(items):
-        ref, _ = orc.iccg(A, bk, bs, 32, box=box, tol=1e-8)
+        ref, _ = orc.iccg(A, bk, bs, w, box=box, tol=1e-8)
         assert ref.status == 0
         assert res.iters[k] == ref.iters, (k, res.iters[k], ref.iters)
         assert _rel(xh[off:off + A.n], ref.x) <= 1e-12
@@ -56,10 +60,11 @@ def test_batch_fp64_matches_oracle_per_system(lib, orc, bs, loop_mode):
     assert np.all(res.solve_ms > 0)
 
 
-def test_batch_fp32_reaches_fp64_tolerance(lib, orc):
+@pytest.mark.parametrize("w", [32, 16])
+def test_batch_fp32_reaches_fp64_tolerance(lib, orc, w):
     items = _small_batch(12, seed0=1100)
     mats = [A for A, _, _ in items]
-    batch = H.hbmc_batch_build(mats, 8, precision=H.PREC_F32)
+    batch = H.hbmc_batch_build(mats, 8, w=w, precision=H.PREC_F32)
     assert H.hbmc_batch_ic0(batch)[0] == H.OK
     b = torch.tensor(_concat(items), device="cuda")
     x = torch.zeros_like(b)
@@ -69,7 +74,7 @@ def test_batch_fp32_reaches_fp64_tolerance(lib, orc):
     xh = x.cpu().numpy()
     off = 0
     for k, (A, bk, _) in enumerate(items):
-        ref, _ = orc.iccg(A, bk, 8, 32, box=(2, 2, 2), tol=1e-8)
+        ref, _ = orc.iccg(A, bk, 8, w, box=(2, 2, 2), tol=1e-8)
         assert abs(int(res.iters[k]) - ref.iters) <= max(2, ref.iters // 10)
         assert _rel(xh[off:off + A.n], ref.x) < 1e-6
         off += A.n
@@ -170,3 +175,23 @@ def test_batch_full_size_sampled(lib, orc):
         ref, _ = orc.iccg(A, bk, 4, 32, box=W.box_for_bs(4), tol=1e-8)
         assert res.iters[k] == ref.iters, (k, res.iters[k], ref.iters)
         assert _rel(xh[offs[k]:offs[k] + A.n], ref.x) <= 1e-12
+
+
+def test_batch_autotune_over_bs_and_w(lib, tmp_path):
+    """The (bs, w) autotuner times every pair, picks the fastest, and a
+    cached choice comes back without timing."""
+    items = _small_batch(16, seed0=1300)
+    mats = [A for A, _, _ in items]
+    b = torch.tensor(_concat(items), device="cuda")
+    cache = str(tmp_path / "tune.txt")
+    bs, w, ms = H.hbmc_batch_autotune_w(mats, b, (4, 8), (16, 32), cache_path=cache)
+    assert ms.shape == (2, 2) and np.all(ms > 0)
+    i, j = (4, 8).index(bs), (16, 32).index(w)
+    assert ms[i, j] == ms.min()
+    bs2, w2, ms2 = H.hbmc_batch_autotune_w(mats, b, (4, 8), (16, 32), cache_path=cache)
+    assert (bs2, w2) == (bs, w) and np.all(ms2 == -1)
+    # the chosen pair solves the batch
+    batch = H.hbmc_batch_build(mats, bs, w=w, precision=H.PREC_F32)
+    assert H.hbmc_batch_ic0(batch)[0] == H.OK
+    x = torch.zeros_like(b)
+    assert H.hbmc_batch_iccg(batch, b, x, tol=1e-8).status == H.OK
