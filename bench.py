@@ -447,14 +447,15 @@ def cpu_baseline(P, gpu_iters, sample_iters):
             "scaled_from_iters": int(s.iters), "sample_s": round(dt, 3), "host": host_info()}
 
 
-def config_solve(P, prec, local, stream, peak, name, reps=5):
+def config_solve(P, prec, local, stream, peak, name, reps=5, loop=None):
     """One configuration: solve time (CUDA events, inputs resident), CG
     iterations, true residual, and the per-sweep device times with their
     algorithmic bandwidth against the measured and the nominal HBM peak."""
     import torch
     from paper_1908_00741_gb300 import hbmc as H
     t = time.perf_counter()
-    ctx = H.hbmc_build(P.A, P.bs, 32, box=P.box, precision=prec, device=local)
+    ctx = H.hbmc_build(P.A, P.bs, 32, box=P.box, precision=prec, device=local,
+                       loop_mode=H.LOOP_GRAPH if loop is None else loop)
     build_s = time.perf_counter() - t
     H.hbmc_set_stream(ctx, stream)
     st, bad = H.hbmc_ic0(ctx)
@@ -489,6 +490,34 @@ def config_solve(P, prec, local, stream, peak, name, reps=5):
                "spmv": {"ms": round(prof["spmv"], 4), "GB/s": round(sp_gbs, 1), **fracs(sp_gbs, peak)}}}
     ctx.close()
     return out
+
+
+def run_config(args):
+    """One of the random-order configurations on its own (config3: the
+    heterogeneous 27-point 96^3 system; config5: the 3-DOF vector Laplacian
+    100^3), FP32 substitutions: the line the default run carries under
+    "configs", with the clocks of its own timed region."""
+    import torch
+    from paper_1908_00741_gb300 import hbmc as H
+    from paper_1908_00741_gb300 import workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    peak, _ = measured_peaks()
+    P, name = ((W.heterogeneous27_problem(args.hetero_m), f"heterogeneous 27-point {args.hetero_m}^3, random order")
+               if args.workload == "config3" else
+               (W.vector_laplacian_problem(args.veclap_m), f"3-DOF vector Laplacian {args.veclap_m}^3 nodes, "
+                                                           "random order"))
+    prec = H.PREC_F64 if args.precision == "f64" else H.PREC_F32
+    with ClockSampler(local) as clk:
+        rep = config_solve(P, prec, local, torch.cuda.current_stream(), peak, name, reps=args.steps,
+                           loop=H.LOOP_HOST if args.loop == "host" else H.LOOP_GRAPH)
+    line = {"metric": METRIC, "value": rep["ms"], "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rep["ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": rep["precision"], "data": "synthetic",
+            "config": {k: rep[k] for k in ("workload", "n", "nnz", "bs", "w", "colors", "precision")},
+            **{k: v for k, v in rep.items() if k not in ("workload", "ms")}, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------
@@ -890,9 +919,10 @@ def run_structural(args):
     with slices of 4 / 8 rows processes about 26% / 39% more entries than CRS,
     the paper's 28% / 40% for Audikw_1), natural order, algebraic blocking
     bs = 8, w = 32.  A step is one hbmc_iccg call with the split SpMV
-    (pieces of 64 entries, piece cost 2); the same solve without splitting,
-    the SpMV alone in both layouts, and the processed entries are reported
-    beside it."""
+    (pieces of 64 entries, piece cost 2); the same solve without splitting
+    and with the variable-slice-height layout (the other remedy, cost 8 per
+    sub-slice), the SpMV alone in each layout, and the processed entries are
+    reported beside it."""
     import torch
     from paper_1908_00741_gb300 import hbmc as H
     from paper_1908_00741_gb300 import workloads as W
@@ -906,8 +936,8 @@ def run_structural(args):
     stream = torch.cuda.current_stream()
     ctxs = {}
     loop = H.LOOP_HOST if args.loop == "host" else H.LOOP_GRAPH
-    for name, split in (("split", piece), ("plain", 0)):
-        c = H.hbmc_build(A, DEFAULT_BS, 32, device=local, sell_split=split, loop_mode=loop)
+    for name, split, vs in (("split", piece, 0), ("plain", 0, 0), ("vslice", 0, 8)):
+        c = H.hbmc_build(A, DEFAULT_BS, 32, device=local, sell_split=split, sell_vslice=vs, loop_mode=loop)
         H.hbmc_set_stream(c, stream)
         st, bad = H.hbmc_ic0(c, 0.0)
         assert st == H.OK, bad
@@ -941,8 +971,8 @@ def run_structural(args):
     # the same solve without row splitting, and both with FP32 substitutions
     others = {}
     for name, c, prec in () if args.no_variants else (
-            ("plain_f64", ctxs["plain"], H.PREC_F64), ("split_f32", ctx, H.PREC_F32),
-            ("plain_f32", ctxs["plain"], H.PREC_F32)):
+            ("plain_f64", ctxs["plain"], H.PREC_F64), ("vslice_f64", ctxs["vslice"], H.PREC_F64),
+            ("split_f32", ctx, H.PREC_F32), ("plain_f32", ctxs["plain"], H.PREC_F32)):
         H.hbmc_set_precision(c, prec)
         for _ in range(2):
             r = solve(c)
@@ -1013,8 +1043,10 @@ def run_structural(args):
         "iters": res.iters, "true_relres": res.true_relres, "max_rel_err_vs_xstar": err,
         "ms_per_iter": round(ms / max(res.iters, 1), 4),
         "processed_entries": {"crs": A.nnz, "sell": inf0["sell_entries_a"], "split": inf["sell_entries_split"],
+                              "vslice": ctxs["vslice"].info()["sell_entries_vslice"],
                               "sell_over_crs": round(inf0["sell_entries_a"] / A.nnz, 4),
                               "split_over_crs": round(inf["sell_entries_split"] / A.nnz, 4),
+                              "vslice_over_crs": round(ctxs["vslice"].info()["sell_entries_vslice"] / A.nnz, 4),
                               "split_rows": inf["split_rows"], "pieces": inf["split_pieces"]},
         "spmv_ms": {k: round(v["spmv"], 4) for k, v in prof.items()},
         "phase_ms": {k: {q: round(t, 4) for q, t in v.items()} for k, v in prof.items()},
@@ -1092,8 +1124,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--bs", type=int, default=DEFAULT_BS)
     ap.add_argument("--workload", default="poisson128",
-                    choices=["poisson128", "batch", "learned", "orderings", "sor", "ilu", "structural"],
-                    help="poisson128: the headline solve; batch: 256 uneven systems solved together; "
+                    choices=["poisson128", "config3", "config5", "batch", "learned", "orderings", "sor", "ilu",
+                             "structural"],
+                    help="poisson128: the headline solve; config3 / config5: the 27-point 96^3 / 3-DOF 100^3 "
+                         "random-order solve (FP32 substitutions unless --precision f64); "
+                         "batch: 256 uneven systems solved together; "
                          "learned: learned IC shift against the plain rule; orderings: MC, BMC and HBMC; "
                          "sor: symmetric SOR sweeps; ilu: ILU(0)-BiCGStab on a nonsymmetric system; "
                          "structural: the row-split SpMV on an Audikw_1-shaped matrix")
@@ -1105,7 +1140,8 @@ def main():
     ap.add_argument("--hetero-m", type=int, default=96)
     ap.add_argument("--curl-m", type=int, default=70)
     ap.add_argument("--batch-systems", type=int, default=256)
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--precision", default=None, choices=["f64", "f32"],
+                    help="substitution precision (default: f64 for poisson128, f32 for config3 / config5)")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="graph: one CUDA graph per solve with a device-side while node; "
                          "host: host-driven iterations (kernels visible to ncu)")
@@ -1117,6 +1153,8 @@ def main():
     ap.add_argument("--ref-sample-iters", type=int, default=10)
     ap.add_argument("--ref-full-iters", type=int, default=124)
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "f32" if args.workload in ("config3", "config5") else "f64"
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
@@ -1124,7 +1162,8 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build()
-        {"batch": run_batch, "learned": run_learned, "orderings": run_orderings,
+        {"batch": run_batch, "learned": run_learned, "orderings": run_orderings, "config3": run_config,
+         "config5": run_config,
          "sor": run_sor, "ilu": run_ilu, "structural": run_structural}.get(args.workload, run_gpu)(args)
 
 

@@ -134,6 +134,16 @@ typedef struct hbmc_options {
                            the SpMV of hbmc_iccg and hbmc_spmv_bar; the residuals and every
                            other kernel keep the unsplit layout.  Needs w = 32 or less. */
   int32_t sell_split_cost; /* the per-piece cost of the plan above, in entries (0 = 2) */
+  int32_t sell_vslice;  /* variable slice height of the CG's SpMV layout (Section 5.2.2 and the
+                           conclusions: the other remedy for SELL's padding).  0 = off
+                           (default).  K > 0: every slice of w rows is cut into w / C
+                           sub-slices of C consecutive rows, C in {w, w/2, w/4}, each padded
+                           only to its own longest row; the slice takes the C minimising
+                             sum over its sub-slices of C * (longest row) + K * (w / C)
+                           (the largest C among equal costs).  Rows keep their order and
+                           every row's terms are summed as in the plain SpMV, so the product
+                           is bit-identical to it.  Used by the SpMV of hbmc_iccg and
+                           hbmc_spmv_bar unless sell_split is set too (row splitting wins). */
 } hbmc_options;
 
 /* Fills *opt with the defaults. */
@@ -162,6 +172,8 @@ typedef struct hbmc_info_t {
   int64_t split_pieces;     /* pieces those rows were cut into */
   int64_t sell_entries_split; /* stored entries of the split SpMV layout: heads plus the
                                  pieces' slices, each with its padding (0 without it) */
+  int64_t sell_entries_vslice; /* stored entries of the variable-slice-height SpMV layout,
+                                  padding included (0 without it) */
 } hbmc_info_t;
 
 /*
@@ -220,6 +232,14 @@ hbmc_status hbmc_get_matrix(const hbmc_ctx *ctx, int64_t *row_ptr, int32_t *col,
  * context was built without row splitting.
  */
 hbmc_status hbmc_get_split(const hbmc_ctx *ctx, int32_t *head);
+
+/*
+ * hbmc_get_vslice - the sub-slice height C of every slice of w rows of the
+ * variable-slice-height SpMV layout (hbmc_options.sell_vslice; Section
+ * 5.2.2): height int32[n_pad / w].  Works for host_only contexts.
+ * INVALID_ARG when the context was built without it.
+ */
+hbmc_status hbmc_get_vslice(const hbmc_ctx *ctx, int32_t *height);
 
 /* Bind the context to a CUDA stream (a cudaStream_t, e.g. from
  * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */

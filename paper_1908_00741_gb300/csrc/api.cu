@@ -134,6 +134,14 @@ hbmc_status upload(hbmc_ctx *ctx) {
     TRY(dupload(ctx, d.cmb_slot, h.cmb_slot));
     TRY(dalloc(ctx, d.tsum, (size_t)std::max<int64_t>(d.n_virt, 1)));
   }
+  if (h.vslice_cost > 0 && h.split_piece <= 0) {
+    d.vslice = 1;
+    TRY(dupload(ctx, d.vs_c, h.vs_c));
+    TRY(dupload(ctx, d.vs_first, h.vs_first));
+    TRY(dupload(ctx, d.vs_ptr, h.vs_ptr));
+    TRY(dupload(ctx, d.vs_col, h.vs_col));
+    TRY(dupload(ctx, d.vs_val, h.vs_val));
+  }
   TRY(dupload(ctx, d.fo_ptr, h.fo_ptr));
   TRY(dupload(ctx, d.fi_ptr, h.fi_ptr));
   TRY(dupload(ctx, d.bo_ptr, h.bo_ptr));
@@ -468,6 +476,7 @@ hbmc_status hbmc_build(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sell_split and sell_split_cost must be >= 0");
   if (o.sell_split > 0 && w > 32)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "row splitting needs w <= 32");
+  if (o.sell_vslice < 0) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sell_vslice must be >= 0");
   if (o.sweep_kernel < 0 || o.sweep_kernel > 8)
     return set_err(nullptr, HBMC_ERR_INVALID_ARG, "sweep_kernel must be in 0..8");
   if (o.sweep_tpb < 0 || (o.sweep_tpb & (o.sweep_tpb - 1)) || (int64_t)o.sweep_tpb * w > 256)
@@ -569,6 +578,7 @@ hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info) {
   info->split_rows = h.split_rows;
   info->split_pieces = h.split_pieces;
   info->sell_entries_split = h.split_piece > 0 ? (int64_t)(h.sh_col.size() + h.sp_col.size()) : 0;
+  info->sell_entries_vslice = h.vslice_cost > 0 ? (int64_t)h.vs_col.size() : 0;
   return HBMC_OK;
 }
 
@@ -577,6 +587,15 @@ hbmc_status hbmc_get_split(const hbmc_ctx *ctx, int32_t *head) {
   const HostLayout &h = ctx->h;
   if (h.split_piece <= 0) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "the context was built without row splitting");
   if (head && !h.split_head.empty()) std::memcpy(head, h.split_head.data(), sizeof(int32_t) * h.split_head.size());
+  return HBMC_OK;
+}
+
+hbmc_status hbmc_get_vslice(const hbmc_ctx *ctx, int32_t *height) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  const HostLayout &h = ctx->h;
+  if (h.vslice_cost <= 0) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "the context was built without sell_vslice");
+  if (height)
+    for (size_t s = 0; s < h.vs_c.size(); ++s) height[s] = h.vs_c[s];
   return HBMC_OK;
 }
 

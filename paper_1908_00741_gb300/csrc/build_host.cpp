@@ -157,6 +157,70 @@ int32_t color_blocks(int64_t n, const int64_t *rp, const int32_t *ci, int64_t nb
 
 }  // namespace
 
+// Variable slice height of the SpMV layout (the other remedy Section 5.2.2
+// and the conclusions name for SELL's padding): each slice of w rows is cut
+// into w / C sub-slices of C consecutive rows, C in {w, w/2, w/4} (C >= 1),
+// each padded only to its own longest row.  The slice takes the C of least
+// cost  sum over its sub-slices of C * (longest row) + cost * (w / C)
+// (padded entries plus a per-sub-slice charge), the largest C among equal
+// costs.  Rows keep their order (no sorting across rows: sigma = C); inside
+// a sub-slice entry t of its row p sits at start + t * C + p.
+hbmc_status plan_vslice(HostLayout &h, int32_t cost, std::string &err) {
+  const int32_t w = h.w;
+  const int64_t ns = h.n_pad / w;
+  const int64_t guard = h.n_pad;
+  h.vslice_cost = cost;
+  h.vs_c.assign(ns, (uint8_t)w);
+  h.vs_first.assign(ns, 0);
+  h.vs_ptr.assign(1, 0);
+  std::vector<int64_t> len(w);
+  for (int64_t s = 0; s < ns; ++s) {
+    for (int32_t j = 0; j < w; ++j) len[j] = h.rp[s * w + j + 1] - h.rp[s * w + j];
+    int32_t c_best = w;
+    int64_t best = -1;
+    for (int32_t C = w; C >= 1 && C >= w / 4; C /= 2) {
+      if (w % C) break;
+      int64_t c = (int64_t)cost * (w / C);
+      for (int32_t k = 0; k < w / C; ++k) {
+        int64_t mx = 0;
+        for (int32_t j = k * C; j < (k + 1) * C; ++j) mx = std::max(mx, len[j]);
+        c += (int64_t)C * mx;
+      }
+      if (best < 0 || c < best) {  // strictly less: ties keep the larger C
+        best = c;
+        c_best = C;
+      }
+      if (C == 1) break;
+    }
+    h.vs_c[s] = (uint8_t)c_best;
+    h.vs_first[s] = (int64_t)h.vs_ptr.size() - 1;
+    for (int32_t k = 0; k < w / c_best; ++k) {
+      int64_t mx = 0;
+      for (int32_t j = k * c_best; j < (k + 1) * c_best; ++j) mx = std::max(mx, len[j]);
+      h.vs_ptr.push_back(h.vs_ptr.back() + mx * c_best);
+    }
+  }
+  if ((int64_t)h.vs_ptr.size() - 1 >= INT32_MAX) {
+    fail(err, "too many sub-slices", (int64_t)h.vs_ptr.size());
+    return HBMC_ERR_INVALID_ARG;
+  }
+  h.vs_col.assign(h.vs_ptr.back(), (int32_t)guard);
+  h.vs_val.assign(h.vs_ptr.back(), 0.0);
+  for (int64_t s = 0; s < ns; ++s) {
+    const int32_t C = h.vs_c[s];
+    for (int32_t j = 0; j < w; ++j) {
+      const int64_t row = s * w + j, sub = h.vs_first[s] + j / C;
+      const int32_t p = j % C;
+      for (int64_t e = h.rp[row], t = 0; e < h.rp[row + 1]; ++e, ++t) {
+        const int64_t slot = h.vs_ptr[sub] + t * C + p;
+        h.vs_col[slot] = h.ci[e];
+        h.vs_val[slot] = h.av[e];
+      }
+    }
+  }
+  return HBMC_OK;
+}
+
 // Row splitting of the SpMV layout (Section 5.2.2: in SELL a slice's rows
 // are padded to its longest row; the remedy is to split rows that are much
 // longer than the others).  Slice s of w rows gets the head width t in
@@ -504,6 +568,10 @@ hbmc_status build_host(int64_t n, const int64_t *rp, const int32_t *ci, const do
 
   if (opt.sell_split > 0) {
     const hbmc_status st = plan_split(h, opt.sell_split, opt.sell_split_cost > 0 ? opt.sell_split_cost : 2, err);
+    if (st != HBMC_OK) return st;
+  }
+  if (opt.sell_vslice > 0) {
+    const hbmc_status st = plan_vslice(h, opt.sell_vslice, err);
     if (st != HBMC_OK) return st;
   }
 

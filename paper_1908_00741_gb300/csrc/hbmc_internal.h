@@ -71,6 +71,15 @@ struct HostLayout {
   std::vector<int32_t> sl_first, cmb_ptr, cmb_slot;
   int64_t split_rows = 0, split_pieces = 0;
 
+  // SpMV with a variable slice height (hbmc_options.sell_vslice): per slice
+  // of w rows its sub-slice height C and first sub-slice; per sub-slice its
+  // start (the width is the length over C); entries column-major per sub-slice.
+  int32_t vslice_cost = 0;
+  std::vector<uint8_t> vs_c;
+  std::vector<int64_t> vs_first, vs_ptr;
+  std::vector<int32_t> vs_col;
+  std::vector<double> vs_val;
+
   // Substitution layouts, one slice per (level-1 block, step).  "o" = entries
   // coupling to other colors (gathered from global memory), "i" = entries
   // coupling to earlier (forward) / later (backward) steps of the same BMC
@@ -258,6 +267,12 @@ struct DeviceLayout {
   uint32_t *sl_mask = nullptr;
   int32_t *sl_first = nullptr, *cmb_ptr = nullptr, *cmb_slot = nullptr;
   double *tsum = nullptr;  // the pieces' sums, n_virt
+  // variable-slice-height SpMV layout (vslice = 1 when built with hbmc_options.sell_vslice)
+  int32_t vslice = 0;
+  uint8_t *vs_c = nullptr;
+  int64_t *vs_first = nullptr, *vs_ptr = nullptr;
+  int32_t *vs_col = nullptr;
+  double *vs_val = nullptr;
   int64_t *fo_ptr = nullptr, *fi_ptr = nullptr, *bo_ptr = nullptr, *bi_ptr = nullptr;
   int32_t *fo_col = nullptr, *bo_col = nullptr;
   uint8_t *fi_m = nullptr, *bi_m = nullptr;

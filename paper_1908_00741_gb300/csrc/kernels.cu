@@ -165,6 +165,52 @@ __global__ void __launch_bounds__(kRowThreads)
   sc->alpha = sc->rho / s;
 }
 
+// Variable-slice-height SpMV (hbmc_options.sell_vslice): row j of slice s
+// lies in sub-slice vs_first[s] + j / C (C = vs_c[s]) at position j % C,
+// its entry t at vs_ptr[sub] + t * C + position.  The row's terms are summed
+// from zero in ascending column order, as in the plain layout, so the
+// product is the same bits; only the padding differs.
+__device__ __forceinline__ double vs_row(const uint8_t *__restrict__ vs_c, const int64_t *__restrict__ vs_first,
+                                         const int64_t *__restrict__ vs_ptr, const int32_t *__restrict__ col,
+                                         const double *__restrict__ val, int w, int lw, int64_t row,
+                                         const double *x) {
+  const int64_t s = row >> lw;
+  const int j = (int)(row & (w - 1));
+  const int C = vs_c[s];
+  const int64_t sub = vs_first[s] + j / C;
+  const int64_t e = vs_ptr[sub + 1];
+  double acc = 0.0;
+  for (int64_t q = vs_ptr[sub] + (j & (C - 1)); q < e; q += C) acc = fma(val[q], __ldg(x + col[q]), acc);
+  return acc;
+}
+
+template <bool kDot>
+__global__ void __launch_bounds__(kRowThreads)
+    k_spmv_vs(const uint8_t *__restrict__ vs_c, const int64_t *__restrict__ vs_first,
+              const int64_t *__restrict__ vs_ptr, const int32_t *__restrict__ col, const double *__restrict__ val,
+              int w, int lw, int64_t n_pad, const double *p, double *q, double *part, Scalars *sc) {
+  if (kDot && sc->done) return;
+  double pq = 0.0;
+  FOR_ROWS(row, n_pad) {
+    const double acc = vs_row(vs_c, vs_first, vs_ptr, col, val, w, lw, row, p);
+    q[row] = acc;
+    if (kDot) pq = fma(p[row], acc, pq);
+  }
+  if (!kDot) return;
+  double v = block_sum<kRowThreads>(pq);
+  if (!publish(part + blockIdx.x, &v, 1, &sc->cnt[CNT_PQ], gridDim.x)) return;
+  const double t = gather_partials<kRowThreads>(part, gridDim.x, 1, 0);
+  if (threadIdx.x != 0) return;
+  sc->cnt[CNT_PQ] = 0;
+  sc->pq = t;
+  if (!(t > 0.0) || !finite(t)) {
+    sc->status = ST_BREAKDOWN;
+    sc->done = 1;
+    return;
+  }
+  sc->alpha = sc->rho / t;
+}
+
 // Row-split SpMV (Section 5.2.2's remedy for slices whose rows differ much
 // in length).  First the pieces: every cut-off piece is a row of its own in
 // a SELL layout of slices of w pieces, summed from zero in ascending column
@@ -673,6 +719,15 @@ void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, c
       k_spmv_split<true><<<row_grid(d), kRowThreads, 0, s>>>(a, d.w, d.lw, d.n_pad, p, q, d.part, d.sc);
     else
       k_spmv_split<false><<<row_grid(d), kRowThreads, 0, s>>>(a, d.w, d.lw, d.n_pad, p, q, d.part, d.sc);
+    return;
+  }
+  if (d.vslice) {
+    if (dot)
+      k_spmv_vs<true><<<row_grid(d), kRowThreads, 0, s>>>(d.vs_c, d.vs_first, d.vs_ptr, d.vs_col, d.vs_val, d.w,
+                                                          d.lw, d.n_pad, p, q, d.part, d.sc);
+    else
+      k_spmv_vs<false><<<row_grid(d), kRowThreads, 0, s>>>(d.vs_c, d.vs_first, d.vs_ptr, d.vs_col, d.vs_val, d.w,
+                                                           d.lw, d.n_pad, p, q, d.part, d.sc);
     return;
   }
   enqueue_spmv_plain(d, p, q, dot, s);

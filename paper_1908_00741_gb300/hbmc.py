@@ -42,7 +42,7 @@ LOOP_PERSISTENT = 2
 
 EXPORTED = [
     "hbmc_default_options", "hbmc_build", "hbmc_destroy", "hbmc_last_error",
-    "hbmc_status_string", "hbmc_info", "hbmc_get_ordering", "hbmc_get_matrix", "hbmc_get_split",
+    "hbmc_status_string", "hbmc_info", "hbmc_get_ordering", "hbmc_get_matrix", "hbmc_get_split", "hbmc_get_vslice",
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
@@ -63,7 +63,7 @@ class Options(ctypes.Structure):
                 ("device", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("sweep_tpb", ctypes.c_int32), ("sweep_kernel", ctypes.c_int32),
                 ("nonsymmetric", ctypes.c_int32), ("sell_split", ctypes.c_int32),
-                ("sell_split_cost", ctypes.c_int32)]
+                ("sell_split_cost", ctypes.c_int32), ("sell_vslice", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -75,7 +75,7 @@ class Info(ctypes.Structure):
                 ("factored", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
                 ("last_iters", ctypes.c_int64), ("last_launches", ctypes.c_int64),
                 ("split_rows", ctypes.c_int64), ("split_pieces", ctypes.c_int64),
-                ("sell_entries_split", ctypes.c_int64)]
+                ("sell_entries_split", ctypes.c_int64), ("sell_entries_vslice", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,6 +112,7 @@ def load():
             "hbmc_get_ordering": (I32, [P, P, P, P, P]),
             "hbmc_get_matrix": (I32, [P, P, P, P]),
             "hbmc_get_split": (I32, [P, P]),
+            "hbmc_get_vslice": (I32, [P, P]),
             "hbmc_set_stream": (I32, [P, P]),
             "hbmc_set_precision": (I32, [P, I32]),
             "hbmc_ic0": (I32, [P, D, P]),
@@ -237,9 +238,11 @@ class Context:
 def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
                loop_mode=LOOP_GRAPH, host_only=False, device=-1, check_every=16,
                sweep_tpb=0, sweep_kernel=0, nonsymmetric=False, sell_split=0,
-               sell_split_cost=0) -> Context:
+               sell_split_cost=0, sell_vslice=0) -> Context:
     """hbmc_build on a CSR (workloads.CSR or any object with n, row_ptr, col, val).
-    sell_split = P > 0 splits the SpMV's long rows into a head and pieces of P."""
+    sell_split = P > 0 splits the SpMV's long rows into a head and pieces of P;
+    sell_vslice = K > 0 gives every SpMV slice its own sub-slice height
+    (cost K entries per sub-slice)."""
     lib = load()
     opt = Options()
     lib.hbmc_default_options(ctypes.byref(opt))
@@ -260,6 +263,7 @@ def hbmc_build(A, bs: int, w: int, *, box=None, grid=None, precision=PREC_F64,
     opt.nonsymmetric = 1 if nonsymmetric else 0
     opt.sell_split = int(sell_split)
     opt.sell_split_cost = int(sell_split_cost)
+    opt.sell_vslice = int(sell_vslice)
     rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(A.col, dtype=np.int32)
     v = np.ascontiguousarray(A.val, dtype=np.float64)
@@ -303,6 +307,14 @@ def hbmc_get_split(ctx: Context):
     head = np.empty(max(inf["n_pad"] // max(inf["w"], 1), 1), dtype=np.int32)
     ctx.check(ctx._lib.hbmc_get_split(ctx.handle, _np_ptr(head)))
     return head[: inf["n_pad"] // max(inf["w"], 1)]
+
+
+def hbmc_get_vslice(ctx: Context):
+    """Sub-slice height C of every slice of w rows of the variable-height SpMV layout."""
+    inf = ctx.info()
+    h = np.empty(max(inf["n_pad"] // max(inf["w"], 1), 1), dtype=np.int32)
+    ctx.check(ctx._lib.hbmc_get_vslice(ctx.handle, _np_ptr(h)))
+    return h[: inf["n_pad"] // max(inf["w"], 1)]
 
 
 def hbmc_set_stream(ctx: Context, stream) -> None:
