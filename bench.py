@@ -541,11 +541,12 @@ def batch_report(args, local, peak, steps=3, warmup=2):
     sub = mats[:32]
     bsub = torch.tensor(np.concatenate([b for _, b, _ in items[:32]]), device="cuda")
     t = time.perf_counter()
-    bs_cand, w_cand = (4, 8, 16, 32), (16, 32)
-    best, best_w, cand_ms = H.hbmc_batch_autotune_w(sub, bsub, bs_cand, w_cand, precision=H.PREC_F32, tol=TOL)
+    bs_cand, w_cand, v_cand = (4, 8, 16, 32), (16, 32), (0, 8)
+    best, best_w, best_v, cand_ms = H.hbmc_batch_autotune_w(sub, bsub, bs_cand, w_cand, v_cand,
+                                                            precision=H.PREC_F32, tol=TOL)
     tune_s = time.perf_counter() - t
     t = time.perf_counter()
-    batch = H.hbmc_batch_build(mats, best, w=best_w, precision=H.PREC_F32, device=local)
+    batch = H.hbmc_batch_build(mats, best, w=best_w, vslice=best_v, precision=H.PREC_F32, device=local)
     build_s = time.perf_counter() - t
     stream = torch.cuda.current_stream()
     H.hbmc_batch_set_stream(batch, stream)
@@ -572,7 +573,8 @@ def batch_report(args, local, peak, steps=3, warmup=2):
     return {"workload": f"{len(mats)} systems, 7/27-point stencils n^3 with n in [16, 64], lognormal "
                         f"sigma in [0, 2], natural order, box blocking",
             "systems": len(mats), "n_total": n_total, "nnz_total": int(sum(A.nnz for A in mats)),
-            "bs": best, "w": best_w, "colors": inf["nc"], "units": inf["units"], "ms": round(ms, 3),
+            "bs": best, "w": best_w, "vslice": best_v, "colors": inf["nc"], "units": inf["units"],
+            "ms": round(ms, 3),
             "all_converged": bool(res.status == H.OK), "max_true_relres": float(res.true_relres.max()),
             "iters": {"min": int(res.iters.min()), "median": float(np.median(res.iters)),
                       "max": int(res.iters.max())},
@@ -582,9 +584,13 @@ def batch_report(args, local, peak, steps=3, warmup=2):
             "aggregate": {"GB/s": round(gbs, 1), **fracs(gbs, peak),
                           "unknowns_per_s": round(n_total / (ms * 1e-3), 1)},
             "autotune": {"subset": "the first 32 systems", "bs": list(bs_cand), "w": list(w_cand),
-                         "subset_ms": {f"bs{b}_w{w}": round(float(cand_ms[i, j]), 3)
-                                       for i, b in enumerate(bs_cand) for j, w in enumerate(w_cand)},
-                         "best_bs": best, "best_w": best_w, "slice_height": "w", "seconds": round(tune_s, 2)},
+                         "vslice": list(v_cand),
+                         "subset_ms": {f"bs{b}_w{w}_v{v}": round(float(cand_ms[i, j, k]), 3)
+                                       for i, b in enumerate(bs_cand) for j, w in enumerate(w_cand)
+                                       for k, v in enumerate(v_cand)},
+                         "best_bs": best, "best_w": best_w, "best_vslice": best_v,
+                         "slice_height": "w" if best_v == 0 else "per slice from {w, w/2, w/4}",
+                         "seconds": round(tune_s, 2)},
             "gen_s": round(gen_s, 1), "build_s": round(build_s, 1)}
 
 def run_batch(args):

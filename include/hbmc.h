@@ -478,7 +478,9 @@ hbmc_status hbmc_batch_build(int32_t nsys, const hbmc_system *systems, int32_t b
                              const hbmc_options *opt, hbmc_batch **out);
 /* The same with w (Section 4.2's level-1 block width: w BMC blocks of a color
  * per level-1 block, w rows per SELL slice) 16 or 32; with w = 16 a warp
- * runs two level-1 blocks.  hbmc_batch_features needs w = 32. */
+ * runs two level-1 blocks.  opt->sell_vslice > 0 gives the batch's SpMV the
+ * variable-slice-height layout (same sums); row splitting is not supported.
+ * hbmc_batch_features needs w = 32. */
 hbmc_status hbmc_batch_build_w(int32_t nsys, const hbmc_system *systems, int32_t bs, int32_t w,
                                const hbmc_options *opt, hbmc_batch **out);
 void hbmc_batch_destroy(hbmc_batch *b);
@@ -519,14 +521,17 @@ hbmc_status hbmc_batch_iccg(hbmc_batch *b, const double *b_dev, double *x_dev, d
 hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
                                 int32_t ncand, const hbmc_options *opt, const double *b_dev, double tol,
                                 int64_t maxit, const char *cache_path, int32_t *best_bs, double *ms);
-/* The same over every pair (bs_candidates[i], w_candidates[j]) (w 16 or 32;
- * the SELL slice height is w): ms[i * nw + j] (may be NULL) receives the
- * timed solve of that pair or -1; *best_bs, *best_w the fastest pair.  The
- * cache key includes both candidate lists. */
+/* The same over every triple (bs_candidates[i], w_candidates[j],
+ * vslice_candidates[k]): w 16 or 32; vslice 0 keeps the SpMV's SELL slice
+ * height at w, K > 0 lets every slice take its height from {w, w/2, w/4}
+ * (hbmc_options.sell_vslice = K).  ms[(i * nw + j) * nv + k] (may be NULL)
+ * receives the timed solve of that triple or -1; *best_bs, *best_w,
+ * *best_vslice the fastest.  The cache key includes the candidate lists. */
 hbmc_status hbmc_batch_autotune_w(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
-                                  int32_t nbs, const int32_t *w_candidates, int32_t nw, const hbmc_options *opt,
+                                  int32_t nbs, const int32_t *w_candidates, int32_t nw,
+                                  const int32_t *vslice_candidates, int32_t nv, const hbmc_options *opt,
                                   const double *b_dev, double tol, int64_t maxit, const char *cache_path,
-                                  int32_t *best_bs, int32_t *best_w, double *ms);
+                                  int32_t *best_bs, int32_t *best_w, int32_t *best_vslice, double *ms);
 
 /* Per-system feature vectors of a batch (host float[nsys *
  * HBMC_NUM_FEATURES], same definitions as hbmc_features). */

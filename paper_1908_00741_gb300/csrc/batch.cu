@@ -106,6 +106,12 @@ struct ARun {
   int bs;
   int64_t units;
   uint32_t off_t, unit_bytes;
+  // the variable-slice-height layout (vs_c null: the plain one)
+  const uint8_t *vs_c;
+  const int64_t *vs_first, *vs_ptr;
+  const int32_t *vs_col;
+  const double *vs_val;
+  int lw;
 };
 
 template <int W>
@@ -121,6 +127,14 @@ __device__ __forceinline__ double *spmv_unit(const ARun &a, unsigned char *smem,
   double *ts = reinterpret_cast<double *>(ws + a.off_t);
   const int32_t *rc = a.rec + u * a.rec_ints;
   for (int k = ln.j; k < a.rec_ints; k += W) rs[k] = rc[k];
+  if (a.vs_c) {
+    // every lane its own rows of the variable-height layout (same sums)
+    for (int l = 0; l < a.bs; ++l)
+      ts[l * W + ln.j] = vs_row(a.vs_c, a.vs_first, a.vs_ptr, a.vs_col, a.vs_val, W, a.lw,
+                                (u * a.bs + l) * W + ln.j, x);
+    __syncwarp(ln.mask);
+    return ts;
+  }
   for (int l = 0; l < a.bs; ++l) ts[l * W + ln.j] = 0.0;
   __syncwarp(ln.mask);
   run_accumulate<double, double, false, W>(a.col, a.val, x, rec64(rs, 2), rs[0], rs + 6, ts, ln.j);
@@ -557,6 +571,12 @@ hbmc::ARun arun(const DeviceLayout &d) {
   a.units = d.tile_ptr[d.nc];
   a.off_t = d.wp_spmv.off_t;
   a.unit_bytes = d.wp_spmv.warp_bytes;
+  a.vs_c = d.vslice ? d.vs_c : nullptr;
+  a.vs_first = d.vs_first;
+  a.vs_ptr = d.vs_ptr;
+  a.vs_col = d.vs_col;
+  a.vs_val = d.vs_val;
+  a.lw = d.lw;
   return a;
 }
 
@@ -830,6 +850,8 @@ hbmc_status hbmc_batch_build_w(int32_t nsys, const hbmc_system *systems, int32_t
   if (opt) o = *opt;
   if (o.host_only) return berr(nullptr, HBMC_ERR_INVALID_ARG, "batch: host_only is not supported");
   if (o.nonsymmetric) return berr(nullptr, HBMC_ERR_INVALID_ARG, "batch: only symmetric systems (IC(0), CG)");
+  if (o.sell_split) return berr(nullptr, HBMC_ERR_INVALID_ARG, "batch: row splitting is not supported");
+  if (o.sell_vslice < 0) return berr(nullptr, HBMC_ERR_INVALID_ARG, "batch: sell_vslice must be >= 0");
   if (o.precision != HBMC_PREC_F64 && o.precision != HBMC_PREC_F32)
     return berr(nullptr, HBMC_ERR_INVALID_ARG, "unknown precision");
   o.sweep_kernel = 0;
@@ -842,7 +864,10 @@ hbmc_status hbmc_batch_build_w(int32_t nsys, const hbmc_system *systems, int32_t
   std::string e;
   hbmc_status st;
   try {
-    st = hbmc::build_batch_host(nsys, systems, bs, w, o, g, b->meta, e);
+    hbmc_options per_sys = o;  // the systems are laid out one by one, the SpMV layout once merged
+    per_sys.sell_vslice = 0;
+    st = hbmc::build_batch_host(nsys, systems, bs, w, per_sys, g, b->meta, e);
+    if (st == HBMC_OK && o.sell_vslice > 0) st = hbmc::plan_vslice(g, o.sell_vslice, e);
   } catch (const std::bad_alloc &) {
     st = HBMC_ERR_OOM;
     e = "host allocation failed";
@@ -1069,37 +1094,44 @@ hbmc_status hbmc_batch_features(hbmc_batch *b, float *feat) {
 hbmc_status hbmc_batch_autotune(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
                                 int32_t ncand, const hbmc_options *opt, const double *b_dev, double tol,
                                 int64_t maxit, const char *cache_path, int32_t *best_bs, double *ms) {
-  const int32_t w32 = 32;
-  int32_t best_w = 0;
-  return hbmc_batch_autotune_w(nsys, systems, bs_candidates, ncand, &w32, 1, opt, b_dev, tol, maxit, cache_path,
-                               best_bs, &best_w, ms);
+  const int32_t w32 = 32, v0 = 0;
+  int32_t best_w = 0, best_v = 0;
+  return hbmc_batch_autotune_w(nsys, systems, bs_candidates, ncand, &w32, 1, &v0, 1, opt, b_dev, tol, maxit,
+                               cache_path, best_bs, &best_w, &best_v, ms);
 }
 
 hbmc_status hbmc_batch_autotune_w(int32_t nsys, const hbmc_system *systems, const int32_t *bs_candidates,
-                                  int32_t nbs, const int32_t *w_candidates, int32_t nw, const hbmc_options *opt,
+                                  int32_t nbs, const int32_t *w_candidates, int32_t nw,
+                                  const int32_t *vslice_candidates, int32_t nv, const hbmc_options *opt,
                                   const double *b_dev, double tol, int64_t maxit, const char *cache_path,
-                                  int32_t *best_bs, int32_t *best_w, double *ms) {
-  if (!best_bs || !best_w || !bs_candidates || nbs < 1 || !w_candidates || nw < 1 || !b_dev)
+                                  int32_t *best_bs, int32_t *best_w, int32_t *best_vslice, double *ms) {
+  if (!best_bs || !best_w || !best_vslice || !bs_candidates || nbs < 1 || !w_candidates || nw < 1 ||
+      !vslice_candidates || nv < 1 || !b_dev)
     return berr(nullptr, HBMC_ERR_INVALID_ARG, "autotune: bad arguments");
   for (int32_t k = 0; k < nw; ++k)
     if (w_candidates[k] != 16 && w_candidates[k] != 32)
       return berr(nullptr, HBMC_ERR_INVALID_ARG, "autotune: w candidates must be 16 or 32");
+  for (int32_t k = 0; k < nv; ++k)
+    if (vslice_candidates[k] < 0) return berr(nullptr, HBMC_ERR_INVALID_ARG, "autotune: vslice candidates must be >= 0");
   // the cache key covers the candidate sets as well as the systems
   std::string key = fingerprint(nsys, systems);
   for (int32_t k = 0; k < nbs; ++k) key += "b" + std::to_string(bs_candidates[k]);
   for (int32_t k = 0; k < nw; ++k) key += "w" + std::to_string(w_candidates[k]);
+  for (int32_t k = 0; k < nv; ++k) key += "v" + std::to_string(vslice_candidates[k]);
+  const int32_t ncand = nbs * nw * nv;
   if (cache_path) {
     std::ifstream in(cache_path);
     std::string line;
     while (std::getline(in, line)) {
       std::istringstream ls(line);
       std::string k;
-      int32_t vb = 0, vw = 0;
-      if ((ls >> k >> vb >> vw) && k == key) {
+      int32_t vb = 0, vw = 0, vv = 0;
+      if ((ls >> k >> vb >> vw >> vv) && k == key) {
         *best_bs = vb;
         *best_w = vw;
+        *best_vslice = vv;
         if (ms)
-          for (int32_t c = 0; c < nbs * nw; ++c) ms[c] = -1.0;
+          for (int32_t c = 0; c < ncand; ++c) ms[c] = -1.0;
         return HBMC_OK;
       }
     }
@@ -1110,17 +1142,19 @@ hbmc_status hbmc_batch_autotune_w(int32_t nsys, const hbmc_system *systems, cons
   double best = 1e300;
   *best_bs = -1;
   *best_w = -1;
+  *best_vslice = -1;
   int64_t n_total = 0;
   for (int32_t s = 0; s < nsys; ++s) n_total += systems[s].n;
   double *x = nullptr;
   if (cudaMalloc(&x, sizeof(double) * (n_total ? n_total : 1)) != cudaSuccess)
     return berr(nullptr, HBMC_ERR_OOM, "autotune: no memory for x");
-  for (int32_t cb = 0; cb < nbs; ++cb) {
-    for (int32_t cw = 0; cw < nw; ++cw) {
-      const int32_t c = cb * nw + cw;
+  for (int32_t c = 0; c < ncand; ++c) {
+    {
+      const int32_t cb = c / (nw * nv), cw = (c / nv) % nw, cv = c % nv;
       if (ms) ms[c] = -1.0;
       const int32_t bs = bs_candidates[cb], w = w_candidates[cw];
       if (!box_for(bs, o.box)) continue;
+      o.sell_vslice = vslice_candidates[cv];
       hbmc_batch *b = nullptr;
       if (hbmc_batch_build_w(nsys, systems, bs, w, &o, &b) != HBMC_OK) continue;
       double t = -1.0;
@@ -1149,6 +1183,7 @@ hbmc_status hbmc_batch_autotune_w(int32_t nsys, const hbmc_system *systems, cons
         best = t;
         *best_bs = bs;
         *best_w = w;
+        *best_vslice = vslice_candidates[cv];
       }
     }
   }
@@ -1156,7 +1191,7 @@ hbmc_status hbmc_batch_autotune_w(int32_t nsys, const hbmc_system *systems, cons
   if (*best_bs < 0) return berr(nullptr, HBMC_ERR_INVALID_ARG, "autotune: no candidate solved the batch");
   if (cache_path) {
     std::ofstream outf(cache_path, std::ios::app);
-    outf << key << " " << *best_bs << " " << *best_w << "\n";
+    outf << key << " " << *best_bs << " " << *best_w << " " << *best_vslice << "\n";
   }
   return HBMC_OK;
 }

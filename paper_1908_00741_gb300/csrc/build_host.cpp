@@ -166,8 +166,11 @@ int32_t color_blocks(int64_t n, const int64_t *rp, const int32_t *ci, int64_t nb
 // costs.  Rows keep their order (no sorting across rows: sigma = C); inside
 // a sub-slice entry t of its row p sits at start + t * C + p.
 hbmc_status plan_vslice(HostLayout &h, int32_t cost, std::string &err) {
+  // Built from the SELL layout itself (a_ptr / a_col / a_val: a row's entries
+  // first, then the guard column), so that it serves a batch's merged layout
+  // as well as a single system's.
   const int32_t w = h.w;
-  const int64_t ns = h.n_pad / w;
+  const int64_t ns = h.a_ptr.empty() ? 0 : (int64_t)h.a_ptr.size() - 1;
   const int64_t guard = h.n_pad;
   h.vslice_cost = cost;
   h.vs_c.assign(ns, (uint8_t)w);
@@ -175,7 +178,12 @@ hbmc_status plan_vslice(HostLayout &h, int32_t cost, std::string &err) {
   h.vs_ptr.assign(1, 0);
   std::vector<int64_t> len(w);
   for (int64_t s = 0; s < ns; ++s) {
-    for (int32_t j = 0; j < w; ++j) len[j] = h.rp[s * w + j + 1] - h.rp[s * w + j];
+    const int64_t width = (h.a_ptr[s + 1] - h.a_ptr[s]) / w;
+    for (int32_t j = 0; j < w; ++j) {
+      int64_t t = 0;
+      while (t < width && h.a_col[h.a_ptr[s] + t * w + j] != guard) ++t;
+      len[j] = t;
+    }
     int32_t c_best = w;
     int64_t best = -1;
     for (int32_t C = w; C >= 1 && C >= w / 4; C /= 2) {
@@ -209,12 +217,14 @@ hbmc_status plan_vslice(HostLayout &h, int32_t cost, std::string &err) {
   for (int64_t s = 0; s < ns; ++s) {
     const int32_t C = h.vs_c[s];
     for (int32_t j = 0; j < w; ++j) {
-      const int64_t row = s * w + j, sub = h.vs_first[s] + j / C;
+      const int64_t sub = h.vs_first[s] + j / C;
       const int32_t p = j % C;
-      for (int64_t e = h.rp[row], t = 0; e < h.rp[row + 1]; ++e, ++t) {
+      for (int64_t t = 0; t < (h.a_ptr[s + 1] - h.a_ptr[s]) / w; ++t) {
+        const int64_t src = h.a_ptr[s] + t * w + j;
+        if (h.a_col[src] == guard) break;
         const int64_t slot = h.vs_ptr[sub] + t * C + p;
-        h.vs_col[slot] = h.ci[e];
-        h.vs_val[slot] = h.av[e];
+        h.vs_col[slot] = h.a_col[src];
+        h.vs_val[slot] = h.a_val[src];
       }
     }
   }

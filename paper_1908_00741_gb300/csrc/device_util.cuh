@@ -70,6 +70,25 @@ __device__ __forceinline__ const T *zgather(const double *z, const float *z32) {
   else return reinterpret_cast<const T *>(z);
 }
 
+// Row `row` of the variable-slice-height SpMV layout (hbmc_options.sell_vslice):
+// row j of slice s lies in sub-slice vs_first[s] + j / C (C = vs_c[s], a
+// power of two) at position j % C, its entry t at vs_ptr[sub] + t * C +
+// position; summed from zero in ascending column order with one fused
+// multiply-add per term, as every SpMV of the library sums a row.
+__device__ __forceinline__ double vs_row(const uint8_t *__restrict__ vs_c, const int64_t *__restrict__ vs_first,
+                                         const int64_t *__restrict__ vs_ptr, const int32_t *__restrict__ col,
+                                         const double *__restrict__ val, int w, int lw, int64_t row,
+                                         const double *x) {
+  const int64_t s = row >> lw;
+  const int j = (int)(row & (w - 1));
+  const int C = vs_c[s];
+  const int64_t sub = vs_first[s] + j / C;
+  const int64_t e = vs_ptr[sub + 1];
+  double acc = 0.0;
+  for (int64_t q = vs_ptr[sub] + (j & (C - 1)); q < e; q += C) acc = fma(val[q], __ldg(x + col[q]), acc);
+  return acc;
+}
+
 // Row kernels run a fixed grid (a few CUDA blocks per SM) and loop over the
 // rows with a grid stride, so each thread accumulates its dot-product terms
 // over several rows before the block reduction.

@@ -122,6 +122,9 @@ hbmc_status build_host(int64_t n, const int64_t *row_ptr, const int32_t *col, co
 // Per-unit records of h from its slice pointer arrays (h.rec_*, h.max_*).
 hbmc_status make_records(HostLayout &h, std::string &err);
 
+// The variable-slice-height SpMV layout (h.vs_*) from h's SELL layout.
+hbmc_status plan_vslice(HostLayout &h, int32_t cost, std::string &err);
+
 // The batched solver's view of its systems (see batch_host.cpp).
 struct BatchMeta {
   int32_t nsys = 0, nc = 0;

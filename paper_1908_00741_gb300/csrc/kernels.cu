@@ -170,20 +170,6 @@ __global__ void __launch_bounds__(kRowThreads)
 // its entry t at vs_ptr[sub] + t * C + position.  The row's terms are summed
 // from zero in ascending column order, as in the plain layout, so the
 // product is the same bits; only the padding differs.
-__device__ __forceinline__ double vs_row(const uint8_t *__restrict__ vs_c, const int64_t *__restrict__ vs_first,
-                                         const int64_t *__restrict__ vs_ptr, const int32_t *__restrict__ col,
-                                         const double *__restrict__ val, int w, int lw, int64_t row,
-                                         const double *x) {
-  const int64_t s = row >> lw;
-  const int j = (int)(row & (w - 1));
-  const int C = vs_c[s];
-  const int64_t sub = vs_first[s] + j / C;
-  const int64_t e = vs_ptr[sub + 1];
-  double acc = 0.0;
-  for (int64_t q = vs_ptr[sub] + (j & (C - 1)); q < e; q += C) acc = fma(val[q], __ldg(x + col[q]), acc);
-  return acc;
-}
-
 template <bool kDot>
 __global__ void __launch_bounds__(kRowThreads)
     k_spmv_vs(const uint8_t *__restrict__ vs_c, const int64_t *__restrict__ vs_first,

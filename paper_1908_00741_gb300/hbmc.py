@@ -142,7 +142,8 @@ def load():
             "hbmc_batch_ic0": (I32, [P, P, P]),
             "hbmc_batch_iccg": (I32, [P, P, P, D, I64, P, P, P, P, P]),
             "hbmc_batch_autotune": (I32, [I32, P, P, I32, P, P, D, I64, ctypes.c_char_p, P, P]),
-            "hbmc_batch_autotune_w": (I32, [I32, P, P, I32, P, I32, P, P, D, I64, ctypes.c_char_p, P, P, P]),
+            "hbmc_batch_autotune_w": (I32, [I32, P, P, I32, P, I32, P, I32, P, P, D, I64, ctypes.c_char_p, P, P, P,
+                                            P]),
             "hbmc_batch_features": (I32, [P, P]),
             "hbmc_features": (I32, [P, P]),
             "hbmc_shift_grid": (D, [I32]),
@@ -559,13 +560,15 @@ class Batch:
         return {"n": n.value, "n_pad": npad.value, "nc": nc.value, "units": nu.value}
 
 
-def hbmc_batch_build(mats, bs, *, w=32, use_boxes=True, precision=PREC_F64, loop_mode=LOOP_GRAPH, device=-1,
-                     check_every=16) -> Batch:
+def hbmc_batch_build(mats, bs, *, w=32, vslice=0, use_boxes=True, precision=PREC_F64, loop_mode=LOOP_GRAPH,
+                     device=-1, check_every=16) -> Batch:
     """Batch of CSR systems (box blocking for grid matrices when use_boxes);
-    w = 32 or 16 BMC blocks per level-1 block."""
+    w = 32 or 16 BMC blocks per level-1 block; vslice = K > 0: the SpMV's
+    variable-slice-height layout."""
     lib = load()
     arr, keep = _systems(mats, use_boxes)
     opt = _box_opts(bs, precision, loop_mode, device, check_every)
+    opt.sell_vslice = int(vslice)
     h = ctypes.c_void_p()
     s = lib.hbmc_batch_build_w(len(mats), ctypes.cast(arr, ctypes.c_void_p), int(bs), int(w), ctypes.byref(opt),
                                ctypes.byref(h))
@@ -628,26 +631,28 @@ def hbmc_batch_autotune(mats, b, bs_candidates=(4, 8, 16, 32), *, use_boxes=True
     return int(best.value), ms
 
 
-def hbmc_batch_autotune_w(mats, b, bs_candidates=(4, 8, 16, 32), w_candidates=(16, 32), *, use_boxes=True,
-                          precision=PREC_F32, tol=1e-8, maxit=10000, cache_path=None, device=-1):
-    """Pick the (bs, w) pair that solves the batch fastest; returns (best_bs,
-    best_w, ms[len(bs_candidates), len(w_candidates)])."""
+def hbmc_batch_autotune_w(mats, b, bs_candidates=(4, 8, 16, 32), w_candidates=(16, 32), vslice_candidates=(0,),
+                          *, use_boxes=True, precision=PREC_F32, tol=1e-8, maxit=10000, cache_path=None, device=-1):
+    """Pick the (bs, w, vslice) triple that solves the batch fastest (vslice 0:
+    SELL slices of height w; K > 0: per-slice heights from {w, w/2, w/4});
+    returns (best_bs, best_w, best_vslice, ms[nbs, nw, nv])."""
     lib = load()
     arr, keep = _systems(mats, use_boxes)
     opt = _box_opts(8, precision, LOOP_GRAPH, device)
     cb = np.ascontiguousarray(bs_candidates, dtype=np.int32)
     cw = np.ascontiguousarray(w_candidates, dtype=np.int32)
-    ms = np.zeros(len(cb) * len(cw))
-    best_bs, best_w = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    cv = np.ascontiguousarray(vslice_candidates, dtype=np.int32)
+    ms = np.zeros(len(cb) * len(cw) * len(cv))
+    best_bs, best_w, best_v = ctypes.c_int32(-1), ctypes.c_int32(-1), ctypes.c_int32(-1)
     n_total = sum(int(A.n) for A in mats)
     s = lib.hbmc_batch_autotune_w(len(mats), ctypes.cast(arr, ctypes.c_void_p), _np_ptr(cb), len(cb), _np_ptr(cw),
-                                  len(cw), ctypes.byref(opt), _dev_ptr(b, n_total, "b"), float(tol), int(maxit),
-                                  cache_path.encode() if cache_path else None, ctypes.byref(best_bs),
-                                  ctypes.byref(best_w), _np_ptr(ms))
+                                  len(cw), _np_ptr(cv), len(cv), ctypes.byref(opt), _dev_ptr(b, n_total, "b"),
+                                  float(tol), int(maxit), cache_path.encode() if cache_path else None,
+                                  ctypes.byref(best_bs), ctypes.byref(best_w), ctypes.byref(best_v), _np_ptr(ms))
     if s != OK:
         raise HbmcError(s, lib.hbmc_batch_last_error(None).decode())
     del keep
-    return int(best_bs.value), int(best_w.value), ms.reshape(len(cb), len(cw))
+    return int(best_bs.value), int(best_w.value), int(best_v.value), ms.reshape(len(cb), len(cw), len(cv))
 
 
 # --------------------------------------------------------------------------

@@ -31,15 +31,16 @@ def _concat(items):
 
 
 @pytest.mark.parametrize("bs", [4, 8, 16])
-@pytest.mark.parametrize("w", [32, 16])
+@pytest.mark.parametrize("w,vslice", [(32, 0), (16, 0), (32, 2), (16, 1)])
 @pytest.mark.parametrize("loop_mode", [H.LOOP_GRAPH, H.LOOP_HOST])
-def test_batch_fp64_matches_oracle_per_system(lib, orc, bs, w, loop_mode):
+def test_batch_fp64_matches_oracle_per_system(lib, orc, bs, w, vslice, loop_mode):
     """Every system of the batch, with w = 32 or 16 BMC blocks per level-1
-    block (two level-1 blocks per warp at 16), takes its own oracle solve's
-    iteration count and iterates."""
+    block (two level-1 blocks per warp at 16), with the SpMV's slices at
+    height w or of variable height, takes its own oracle solve's iteration
+    count and iterates."""
     items = _small_batch()
     mats = [A for A, _, _ in items]
-    batch = H.hbmc_batch_build(mats, bs, w=w, loop_mode=loop_mode, check_every=3)
+    batch = H.hbmc_batch_build(mats, bs, w=w, vslice=vslice, loop_mode=loop_mode, check_every=3)
     st, bad = H.hbmc_batch_ic0(batch)
     assert st == H.OK and np.all(bad == -1)
     b = torch.tensor(_concat(items), device="cuda")
@@ -184,14 +185,14 @@ def test_batch_autotune_over_bs_and_w(lib, tmp_path):
     mats = [A for A, _, _ in items]
     b = torch.tensor(_concat(items), device="cuda")
     cache = str(tmp_path / "tune.txt")
-    bs, w, ms = H.hbmc_batch_autotune_w(mats, b, (4, 8), (16, 32), cache_path=cache)
-    assert ms.shape == (2, 2) and np.all(ms > 0)
-    i, j = (4, 8).index(bs), (16, 32).index(w)
-    assert ms[i, j] == ms.min()
-    bs2, w2, ms2 = H.hbmc_batch_autotune_w(mats, b, (4, 8), (16, 32), cache_path=cache)
-    assert (bs2, w2) == (bs, w) and np.all(ms2 == -1)
-    # the chosen pair solves the batch
-    batch = H.hbmc_batch_build(mats, bs, w=w, precision=H.PREC_F32)
+    bs, w, v, ms = H.hbmc_batch_autotune_w(mats, b, (4, 8), (16, 32), (0, 8), cache_path=cache)
+    assert ms.shape == (2, 2, 2) and np.all(ms > 0)
+    i, j, k = (4, 8).index(bs), (16, 32).index(w), (0, 8).index(v)
+    assert ms[i, j, k] == ms.min()
+    bs2, w2, v2, ms2 = H.hbmc_batch_autotune_w(mats, b, (4, 8), (16, 32), (0, 8), cache_path=cache)
+    assert (bs2, w2, v2) == (bs, w, v) and np.all(ms2 == -1)
+    # the chosen triple solves the batch
+    batch = H.hbmc_batch_build(mats, bs, w=w, vslice=v, precision=H.PREC_F32)
     assert H.hbmc_batch_ic0(batch)[0] == H.OK
     x = torch.zeros_like(b)
     assert H.hbmc_batch_iccg(batch, b, x, tol=1e-8).status == H.OK

@@ -1,7 +1,8 @@
 """The variable-slice-height SpMV (hbmc_options.sell_vslice) on the GPU:
 the product bit-equal to the oracle's SpMV (same terms, same order; only
-the padding differs), and a solve with it bit-equal to the solve with the
-plain layout."""
+the padding differs), and a solve with it taking the plain layout's
+iteration count with iterates within 1e-12 (its p.q is reduced in its own
+kernel's order, like every SpMV variant's)."""
 import numpy as np
 import pytest
 import torch
@@ -46,7 +47,7 @@ def test_vslice_spmv_bitwise_and_solve(lib, orc, name, mk, bs, w, box, K):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(q.cpu().numpy(), orc.spmv(an.row_ptr, an.col, an.val, r))
     assert np.any(H.hbmc_get_vslice(ctx) < w) or "poisson" in name
-    # the solve with it equals the solve with the plain layout bit for bit
+    # the solve with it: the plain layout's iteration count, iterates within 1e-12
     shift = 0.3 if "curlcurl" in name else 0.0
     b, _ = W.rhs_from_solution(A, 0)
     xs = []
@@ -57,7 +58,7 @@ def test_vslice_spmv_bitwise_and_solve(lib, orc, name, mk, bs, w, box, K):
         assert res.status == H.OK
         xs.append((res.iters, x.cpu().numpy()))
     assert xs[0][0] == xs[1][0]
-    np.testing.assert_array_equal(xs[0][1], xs[1][1])
+    assert np.max(np.abs(xs[0][1] - xs[1][1])) <= 1e-12 * np.max(np.abs(xs[1][1]))
 
 
 def test_vslice_full_size_structural(lib, orc):
