@@ -189,7 +189,7 @@ struct WidePlan {
 // offsets; ok = false when a level-1 block's runs do not fit.
 struct DagPlan {
   uint32_t off_xr = 0, off_ts = 0, off_tin = 0, off_ds = 0, off_rr = 0, off_oc = 0, off_vv = 0, off_iv = 0,
-           off_im = 0, smem_bytes = 0;
+           off_im = 0, off_pos = 0, smem_bytes = 0;
   bool ok = false;
 };
 

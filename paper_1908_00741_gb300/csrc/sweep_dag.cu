@@ -16,12 +16,18 @@
 //     block reads that no other level-1 block of this sweep writes: record,
 //     right-hand side, dinv, r (backward, for the fused r.z), the row offsets,
 //     columns and coefficients of the other-color run and the same-block run;
-//   - it then waits (acquire loads, bounded by %globaltimer) until every
-//     level-1 block on its host-built dependency list has published the
-//     current sweep's epoch, gathers the vector entries those rows hold (L2
-//     loads, one thread per row, eight gathers in flight), adds its terms,
-//     runs the bs-step chains of Eqs. "y2-2" / "y2-3", stores its rows and
-//     publishes its own epoch with a release store.
+//   - once they have landed, it gathers in rounds.  A row's other-color
+//     terms are stored in sweep order (forward: ascending column, i.e.
+//     earlier colors first; backward: descending), and the dependency list
+//     is sorted the same way, so whatever prefix of the list is already
+//     published covers a prefix of every row's terms.  Warp 0 polls the list
+//     (acquire loads, bounded by %globaltimer) and publishes the first row
+//     index that is not yet readable; every thread then adds its row's terms
+//     up to that bound (L2 gathers, one thread per row, several in flight)
+//     and the next round waits for the list to grow.  Only the terms of the
+//     colors published last are left for the round after the final wait;
+//   - it then runs the bs-step chains of Eqs. "y2-2" / "y2-3", stores its
+//     rows and publishes its own epoch with a release store.
 // The epoch of a launch is ticket / (level-1 blocks) + 1: every launch takes
 // exactly one ticket per level-1 block, so counter and flags never need
 // resetting.  Per-row term order and arithmetic are those of every other
@@ -51,9 +57,10 @@ constexpr int kDagGather = 16;         // gathers in flight per thread
 // one color waits for that whole color (one counter) instead of their flags.
 constexpr int64_t kDagColorWait = 16;
 constexpr int kDagChain = 4;  // same-block terms loaded together in a chain step
+constexpr unsigned kDagPollCheck = 64;  // polls between looks at the abort word and the clock
 constexpr int kDagMinBlocks = 3;
 constexpr int kDagAutoColors = 8;               // automatic selection: at least this many colors
-constexpr uint32_t kDagAutoSmem = 110 * 1024;   // ... and two CUDA blocks per SM  // resident CUDA blocks per SM the registers are cut for
+constexpr uint32_t kDagAutoSmem = 110 * 1024;   // ... and two CUDA blocks per SM
 
 template <typename T>
 struct DagArgs {
@@ -70,6 +77,7 @@ struct DagArgs {
   const int32_t *dep;      //   v >= 0: level-1 block v; v < 0: every level-1 block of color -v-1
   const int32_t *unit_color;   // level-1 block -> color
   const int64_t *color_units;  // color -> its level-1 blocks
+  const int64_t *color_first;  // color -> its first level-1 block (n_c + 1 entries)
   unsigned *flag;          // per level-1 block: epoch of its last published result
   unsigned *color_done;    // per color: level-1 blocks published in this launch
   const uint8_t *counted;  // per color: some level-1 block waits on its counter
@@ -81,7 +89,7 @@ struct DagArgs {
   int64_t stall;     // test hook: this level-1 block never publishes (-1: none)
   uint64_t wait_ns;  // bound of every wait
   int rec_ints, bs, x_stride;
-  uint32_t off_xr, off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_iv, off_im;
+  uint32_t off_xr, off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_iv, off_im, off_pos;
 };
 
 // Gathers go through L1: the rows of a level-1 block share many columns (a
@@ -160,6 +168,77 @@ __device__ __forceinline__ void dag_chain(int bs, const int32_t *__restrict__ i_
   }
 }
 
+// Warp 0 (all 32 lanes) moves kd over the satisfied prefix of the
+// dependency list [kd, kend): it ends at the first dependency whose rows are
+// not all published in this launch (kend when every one is).  With `block`
+// it waits until the prefix has grown (or is complete).  Returns false when
+// the wait ran out (then it raises the launch's abort word and the solve's
+// timeout) or another CUDA block of the launch gave up.
+//
+// The list is taken 32 entries at a time, one per lane; each lane keeps its
+// entry's address and target in registers, so a poll is one load per lane
+// (a per-block flag or a per-color counter), and the abort word and the
+// clock are read only every kDagPollCheck polls.
+template <typename T>
+__device__ __forceinline__ bool dag_advance(const DagArgs<T> &a, int64_t &kd, int64_t kend, unsigned epoch,
+                                            bool block, uint64_t deadline, int lane, Scalars *sc) {
+  const int64_t k0 = kd;
+  while (kd < kend) {
+    const int64_t q = kd + lane;
+    const unsigned *f = nullptr;
+    unsigned target = 0;
+    bool is_flag = true;
+    if (q < kend) {
+      const int32_t v = a.dep[q];
+      is_flag = v >= 0;
+      f = is_flag ? a.flag + v : a.color_done + (-v - 1);
+      target = is_flag ? epoch : (unsigned)a.color_units[-v - 1];
+    }
+    for (unsigned spins = 1;; ++spins) {
+      bool sat = true;
+      if (f) {
+        const unsigned x = ld_relaxed_gpu(f);
+        sat = is_flag ? (int)(x - target) >= 0 : x >= target;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, sat);
+      if (m == 0xffffffffu) {  // the whole window: go on with the next one
+        kd = kd + 32 < kend ? kd + 32 : kend;
+        break;
+      }
+      const int first = __ffs(~m) - 1;
+      if (first > 0 || kd > k0 || !block) {
+        kd += first;
+        return true;
+      }
+      if (spins % kDagPollCheck == 0) {
+        if (__any_sync(0xffffffffu, ld_relaxed_gpu(a.abort) == epoch)) return false;  // another CUDA block gave up
+        if (__any_sync(0xffffffffu, global_ns() > deadline)) {
+          if (lane == 0) {
+            *(volatile unsigned *)a.abort = epoch;
+            sc->timeout = 1;
+            sc->done = 1;
+          }
+          return false;
+        }
+      }
+    }
+  }
+  return true;
+}
+
+// The row bound that goes with the first unsatisfied dependency kd: forward,
+// rows below it are readable (the dependency's first row); backward, rows
+// from it on (the row after the dependency's last one).  All readable when
+// the list is exhausted.
+template <bool FWD, typename T>
+__device__ __forceinline__ int64_t dag_bound(const DagArgs<T> &a, int64_t kd, int64_t kend, int64_t R) {
+  if (kd >= kend) return FWD ? INT64_MAX : (int64_t)-1;
+  const int32_t v = a.dep[kd];
+  if (v >= 0) return (FWD ? (int64_t)v : (int64_t)v + 1) * R;
+  const int c = -v - 1;
+  return (FWD ? a.color_first[c] : a.color_first[c + 1]) * R;
+}
+
 // One level-1 block of a sweep.  Returns the ticket position k (>= 0) when
 // the block's rows were computed and published, -1 when the CUDA block left
 // early (the solve was already over, or a wait ran out).
@@ -225,64 +304,85 @@ __device__ __forceinline__ int64_t dag_unit(const DagArgs<T> &a, unsigned char *
       tma_load_1d(im, a.i_m + ibeg, (uint32_t)ilen, bar);
     }
   }
-  // Wait for what this level-1 block gathers from: one warp polls the
-  // dependency list (relaxed loads, then a fence: the acquire side of the
-  // producers' fence and store).
+  // The first look at the dependency list overlaps the copies; later rounds
+  // wait for it to grow.
+  __shared__ int64_t s_bound[2];
+  __shared__ int s_state[2];  // 1: every dependency published; 0: more to come; -1: give up
   const uint64_t deadline = global_ns() + a.wait_ns;
-  int ok = 1;
+  int64_t kd = a.dep_ptr[u];
+  const int64_t kend = a.dep_ptr[u + 1];
   if (tid < 32) {
-    const int64_t d1 = a.dep_ptr[u + 1];
-    for (int64_t q = a.dep_ptr[u] + tid; q < d1 && ok; q += 32) {
-      const int32_t v = a.dep[q];
-      const unsigned *f = v >= 0 ? a.flag + v : a.color_done + (-v - 1);
-      const unsigned target = v >= 0 ? epoch : (unsigned)a.color_units[-v - 1];
-      for (;;) {
-        const unsigned x = ld_relaxed_gpu(f);
-        if (v >= 0 ? (int)(x - epoch) >= 0 : x >= target) break;
-        if (ld_relaxed_gpu(a.abort) == epoch) {  // another CUDA block of this launch gave up
-          ok = 0;
-          break;
-        }
-        if (global_ns() > deadline) {
-          *(volatile unsigned *)a.abort = epoch;
-          sc->timeout = 1;
-          sc->done = 1;
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
+    dag_advance<T>(a, kd, kend, epoch, false, deadline, tid, sc);  // does not wait, cannot fail
+    __threadfence();  // acquire: the flags and counters read above before the gathers below
+    if (tid == 0) {
+      s_state[0] = kd >= kend ? 1 : 0;
+      s_bound[0] = dag_bound<FWD, T>(a, kd, kend, (int64_t)R);
     }
-    __threadfence();
   }
-  const bool landed = mbar_wait(bar, 0, deadline + a.wait_ns);
-  if (!__syncthreads_and(ok && landed)) {
-    if (!landed) {
+  const bool landed = mbar_wait(bar, 0, deadline);
+  if (!__syncthreads_and(landed)) {
+    if (tid == 0) {
       *(volatile unsigned *)a.abort = epoch;
       sc->timeout = 1;
       sc->done = 1;
+      mbar_wait(bar, 0, deadline + a.wait_ns);  // let every copy land before the CUDA block leaves
     }
-    // let every copy land before the CUDA block leaves
-    if (tid == 0) mbar_wait(bar, 0, deadline + 2 * a.wait_ns);
     __syncthreads();
     return -1;
   }
-  // One thread per row: the row's other-color terms in the layout's order,
-  // kDagGather gathers in flight.
+  int32_t *pos = reinterpret_cast<int32_t *>(smem + a.off_pos);
   for (int lr = tid; lr < (int)R; lr += NT) {
-    T acc = (T)tin[lr];
-    int p = xr[lr];
-    const int pe = xr[lr + 1];
-    for (; p < pe; p += kDagGather) {
-      T g[kDagGather];
-#pragma unroll
-      for (int q = 0; q < kDagGather; ++q)
-        if (p + q < pe) g[q] = (T)gather(gsrc + oc[p + q]);
-#pragma unroll
-      for (int q = 0; q < kDagGather; ++q)
-        if (p + q < pe) acc = fma(-vv[p + q], g[q], acc);
+    ts[lr] = (T)tin[lr];
+    pos[lr] = xr[lr];
+  }
+  for (int round = 0;; ++round) {
+    if (round > 0) {
+      if (tid < 32) {
+        // the previous round took everything that was readable: wait for more
+        const bool ok = dag_advance<T>(a, kd, kend, epoch, true, deadline, tid, sc);
+        __threadfence();
+        if (tid == 0) {
+          s_state[round & 1] = ok ? (kd >= kend ? 1 : 0) : -1;
+          s_bound[round & 1] = dag_bound<FWD, T>(a, kd, kend, (int64_t)R);
+        }
+      }
+      // Double-buffered by round: a thread reads round r's entry after the
+      // barrier that follows its writing, and warp 0 writes that entry again
+      // only in round r + 2, after the barrier of round r + 1.
+      __syncthreads();
     }
-    ts[lr] = acc;
+    const int st = s_state[round & 1];
+    if (st < 0) return -1;  // every copy has landed
+    const int64_t bound = s_bound[round & 1];
+    // One thread per row (the same rows every round): the row's readable
+    // other-color terms in the layout's order, kDagGather gathers in flight.
+    for (int lr = tid; lr < (int)R; lr += NT) {
+      int p = pos[lr];
+      const int pe = xr[lr + 1];
+      int pr = pe;  // the last round: every remaining term is readable
+      if (st != 1) {
+        pr = p;
+        if constexpr (FWD) {
+          while (pr < pe && (int64_t)oc[pr] < bound) ++pr;
+        } else {
+          while (pr < pe && (int64_t)oc[pr] >= bound) ++pr;
+        }
+      }
+      if (pr == p) continue;
+      T acc = ts[lr];
+      for (; p < pr; p += kDagGather) {
+        T g[kDagGather];
+#pragma unroll
+        for (int q = 0; q < kDagGather; ++q)
+          if (p + q < pr) g[q] = (T)gather(gsrc + oc[p + q]);
+#pragma unroll
+        for (int q = 0; q < kDagGather; ++q)
+          if (p + q < pr) acc = fma(-vv[p + q], g[q], acc);
+      }
+      ts[lr] = acc;
+      pos[lr] = pr;
+    }
+    if (st == 1) break;
   }
   __syncthreads();
   // The chains on warp 0, then the publication.
@@ -358,7 +458,8 @@ DagPlan plan_one(int bs, int w, bool fwd, int rec_ints, int64_t max_x, int64_t m
   p.off_vv = a16(p.off_oc + (uint64_t)max_x * 4);
   p.off_iv = a16(p.off_vv + (uint64_t)max_x * tsize);
   p.off_im = a16(p.off_iv + (uint64_t)max_i * tsize);
-  const uint64_t total = a16(p.off_im + (uint64_t)max_i);
+  p.off_pos = a16(p.off_im + (uint64_t)max_i);
+  const uint64_t total = a16(p.off_pos + R * 4);
   p.smem_bytes = (uint32_t)std::min<uint64_t>(total, 0xffffffffu);
   p.ok = w == 32 && rec_ints <= (int)kDagRecInts && total <= kDagSmemBudget;
   return p;
@@ -393,6 +494,7 @@ DagArgs<T> dag_args(const DeviceLayout &d, bool fwd, const DagPlan &p) {
   a.flag = fwd ? d.dag_flag_f : d.dag_flag_b;
   a.unit_color = d.dag_unit_color;
   a.color_units = d.dag_color_units;
+  a.color_first = d.tile_ptr_dev;
   a.color_done = fwd ? d.dag_color_done : d.dag_color_done + d.nc;
   a.counted = d.dag_counted + (fwd ? 0 : d.nc);
   a.exit_cnt = d.dag_exit + (fwd ? 0 : 1);
@@ -412,6 +514,7 @@ DagArgs<T> dag_args(const DeviceLayout &d, bool fwd, const DagPlan &p) {
   a.off_vv = p.off_vv;
   a.off_iv = p.off_iv;
   a.off_im = p.off_im;
+  a.off_pos = p.off_pos;
   return a;
 }
 
@@ -422,21 +525,32 @@ cudaError_t allow(K kernel) {
 
 // Per level-1 block, what it waits for: the level-1 blocks holding the rows
 // its other-color couplings read (the run's padding points past the last
-// row and is skipped), ascending -- except that where it reads more than
-// kDagColorWait level-1 blocks of one color it waits for that whole color,
-// entry -(color + 1): in a random input order a level-1 block reads a third
-// of the level-1 blocks of each of several earlier colors, and one counter
-// per color is far cheaper to poll than hundreds of flags.
-void deps_of(const HostLayout &h, const std::vector<int64_t> &xp, const std::vector<int32_t> &xc,
+// row and is skipped) -- except that where it reads more than kDagColorWait
+// level-1 blocks of one color it waits for that whole color, entry
+// -(color + 1): in a random input order a level-1 block reads a third of the
+// level-1 blocks of each of several earlier colors, and one counter per
+// color is far cheaper to poll than hundreds of flags.  The list is sorted
+// in the order the row terms are stored (forward: by first row ascending;
+// backward: by last row descending), so that a satisfied prefix of it makes
+// a prefix of every row's terms readable.
+void deps_of(const HostLayout &h, bool fwd, const std::vector<int64_t> &xp, const std::vector<int32_t> &xc,
              const std::vector<int32_t> &ucolor, std::vector<int64_t> &ptr, std::vector<int32_t> &dep) {
   const int64_t R = (int64_t)h.bs * h.w;
   ptr.assign((size_t)h.ntiles + 1, 0);
   dep.clear();
   std::vector<int64_t> mark((size_t)h.ntiles, -1);
-  std::vector<int32_t> units;
+  std::vector<int32_t> units, list;
   std::vector<int64_t> per_color((size_t)h.nc, 0);
+  // sort key: the first level-1 block of an entry (forward), minus the one
+  // after its last (backward)
+  auto key = [&](int32_t v) -> int64_t {
+    if (v >= 0) return fwd ? (int64_t)v : -((int64_t)v + 1);
+    const int c = -v - 1;
+    return fwd ? h.tile_ptr[c] : -h.tile_ptr[c + 1];
+  };
   for (int64_t u = 0; u < h.ntiles; ++u) {
     units.clear();
+    list.clear();
     for (int64_t e = xp[u]; e < xp[u + 1]; ++e) {
       const int64_t c = xc[(size_t)e];
       if (c < 0 || c >= h.n_pad) continue;
@@ -446,13 +560,14 @@ void deps_of(const HostLayout &h, const std::vector<int64_t> &xp, const std::vec
         units.push_back((int32_t)v);
       }
     }
-    std::sort(units.begin(), units.end());
     for (int32_t v : units) ++per_color[(size_t)ucolor[(size_t)v]];
     for (int c = 0; c < h.nc; ++c)
-      if (per_color[(size_t)c] > kDagColorWait) dep.push_back(-(c + 1));
+      if (per_color[(size_t)c] > kDagColorWait) list.push_back(-(c + 1));
     for (int32_t v : units)
-      if (per_color[(size_t)ucolor[(size_t)v]] <= kDagColorWait) dep.push_back(v);
+      if (per_color[(size_t)ucolor[(size_t)v]] <= kDagColorWait) list.push_back(v);
     for (int32_t v : units) per_color[(size_t)ucolor[(size_t)v]] = 0;
+    std::sort(list.begin(), list.end(), [&](int32_t x, int32_t y) { return key(x) < key(y); });
+    dep.insert(dep.end(), list.begin(), list.end());
     ptr[(size_t)u + 1] = (int64_t)dep.size();
   }
 }
@@ -469,8 +584,8 @@ bool dag_host_tables(const HostLayout &h, DagTables &t) {
     t.color_units[(size_t)c] = h.tile_ptr[c + 1] - h.tile_ptr[c];
     for (int64_t u = h.tile_ptr[c]; u < h.tile_ptr[c + 1]; ++u) t.ucolor[(size_t)u] = c;
   }
-  deps_of(h, h.fx_ptr, h.fx_col, t.ucolor, t.ptr_f, t.dep_f);
-  deps_of(h, h.bx_ptr, h.bx_col, t.ucolor, t.ptr_b, t.dep_b);
+  deps_of(h, true, h.fx_ptr, h.fx_col, t.ucolor, t.ptr_f, t.dep_f);
+  deps_of(h, false, h.bx_ptr, h.bx_col, t.ucolor, t.ptr_b, t.dep_b);
   t.counted.assign(2 * (size_t)h.nc, 0);
   for (int dir = 0; dir < 2; ++dir)
     for (int32_t v : dir == 0 ? t.dep_f : t.dep_b)
@@ -487,6 +602,7 @@ void plan_dag_kernels(const HostLayout &h, DeviceLayout &d) {
   d.dg_f64_b = plan_one(h.bs, h.w, false, h.rec_ints, h.max_x_b, h.max_i_b, 8);
   d.dg_f32_f = plan_one(h.bs, h.w, true, h.rec_ints, h.max_x_f, h.max_i_f, 4);
   d.dg_f32_b = plan_one(h.bs, h.w, false, h.rec_ints, h.max_x_b, h.max_i_b, 4);
+
 }
 
 template <int BS>
@@ -505,7 +621,7 @@ cudaError_t setup_dag_kernels() {
 }
 
 bool dag_usable(const DeviceLayout &d, bool fwd, int prec) {
-  return d.w == 32 && d.rec_f && d.dag_ticket && d.dag_color_done && (fwd ? d.dep_ptr_f : d.dep_ptr_b) &&
+  return d.w == 32 && d.rec_f && d.dag_ticket && d.dag_color_done && d.tile_ptr_dev && (fwd ? d.dep_ptr_f : d.dep_ptr_b) &&
          (fwd || d.dag_order_b) && dag_plan(d, fwd, prec).ok;
 }
 
