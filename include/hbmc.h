@@ -424,10 +424,11 @@ hbmc_status hbmc_sor_bar(hbmc_ctx *ctx, const double *b_dev, double *x_dev, doub
  * hbmc_spmv_dot_static - q = Abar p and p.q without allocating anything.
  *
  * The paper has no counterpart: this exists for callers that cannot
- * allocate device memory when they need the product, such as code running
- * while a stream is captured into a CUDA graph (cudaMalloc is not allowed
- * then), programs whose device memory belongs entirely to another allocator,
- * or loops that must not allocate after start-up.  It computes what the
+ * allocate device memory when they need the product: programs whose device
+ * memory belongs entirely to another allocator (a framework's caching
+ * allocator with a fixed budget, so a cudaMalloc of our own could fail or
+ * fragment its pool), and time-critical loops that must not allocate after
+ * start-up (cudaMalloc may synchronize the device).  It computes what the
  * solver's unsplit SpMV computes (same bits in q; with sell_split the
  * solver's product is the row-split one instead), but keeps its reduction scratch
  * in a fixed array of static device memory inside the library: 16 bytes plus

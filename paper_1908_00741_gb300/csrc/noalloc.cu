@@ -1,11 +1,11 @@
 // hbmc_spmv_dot_static: q = Abar p and p.q with no allocation at all.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// product: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not permitted there), programs whose device memory is
-// entirely owned by another allocator (for instance a framework's caching
-// allocator with a fixed budget), and latency-critical loops that forbid
-// allocation after start-up.  This entry point serves them.  It is the
+// product: programs whose device memory is entirely owned by another
+// allocator (for instance a framework's caching allocator with a fixed
+// budget, where a cudaMalloc of our own could fail or fragment its pool),
+// and latency-critical loops that forbid allocation after start-up
+// (cudaMalloc may synchronize the device).  This entry point serves them.  It is the
 // warp-per-level-1-block SpMV with the fused p.q of the solver, except that
 // its reduction scratch (one partial sum per CUDA block and an arrival
 // counter) lives in a fixed-size array in the library's own static device

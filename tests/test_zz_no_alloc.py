@@ -1,6 +1,6 @@
 """hbmc_spmv_dot_static: the SpMV with fused p.q for callers that cannot
-allocate device memory (stream capture in progress, a device owned by
-another allocator, loops that must not allocate).  Its scratch is a static
+allocate device memory (a device whose memory another allocator owns, loops
+that must not allocate after start-up).  Its scratch is a static
 array inside the library; these tests check it against the solver's own
 SpMV entry point, twice in a row (the array is reused and must be cleared
 between calls), and that oversized systems are refused.
