@@ -587,9 +587,11 @@ hbmc_status hbmc_mlp_gradient(hbmc_mlp *net, const float *X_dev, const float *T_
  * *loss (may be NULL) receives L after training. */
 hbmc_status hbmc_mlp_train(hbmc_mlp *net, const float *X_dev, const float *T_dev, int32_t B, int32_t steps,
                            float lr, float *loss);
-/* Learned shift for ctx's matrix: the grid shift with the lowest predicted
- * iterations; predicted (host float[HBMC_SHIFT_GRID], may be NULL) gets the
- * network's outputs.  Needs a network with in_dim = HBMC_NUM_FEATURES + 1. */
+/* Learned shift for ctx's matrix: the grid shift with the lowest network
+ * output (the predicted cost of each grid shift: log2 of its CG iterations
+ * relative to the matrix's best, as learned_shift.py trains it); predicted
+ * (host float[HBMC_SHIFT_GRID], may be NULL) gets the network's outputs.
+ * Needs a network with in_dim = HBMC_NUM_FEATURES + 1. */
 hbmc_status hbmc_predict_shift(hbmc_ctx *ctx, hbmc_mlp *net, double *shift, float *predicted);
 /* Factor ctx with the learned shift (net != NULL) or the plain rule (net ==
  * NULL).  If the learned shift's IC(0) fails, the plain rule continues from

@@ -2,9 +2,10 @@
 
 Orchestration only: the sweeps are batched HBMC-ICCG solves, the features
 come from the library's feature kernel, and training is the library's
-forward/backward/Adam kernels (hbmc_mlp_train).  The network predicts
-log2(CG iterations) from [features, shift code]; the shift it recommends is
-the grid shift with the lowest prediction.  The plain positive-pivot rule
+forward/backward/Adam kernels (hbmc_mlp_train).  The network predicts,
+from [features, shift code], log2 of the CG iterations at that shift over
+the system's least over the grid; the shift it recommends is the grid shift
+with the lowest prediction.  The plain positive-pivot rule
 (hbmc_ic0_auto without a network) remains the fallback when the predicted
 shift's factorization fails, and the yardstick the learned choice is
 measured against.
@@ -75,16 +76,25 @@ def best_choice(sw: Sweep, s):
 
 
 def dataset(sw: Sweep):
-    """Inputs [features, shift code] and targets log2(iterations) for every
-    (system, shift) pair of systems with at least one converged shift."""
+    """Inputs [features, shift code] and targets for every (system, shift)
+    pair of systems with at least one converged shift: log2 of the shift's
+    cost over the system's least cost among the shifts whose IC(0) works.
+    The choice only needs the shape of each system's cost curve; a target
+    relative to its minimum spares the network from predicting the absolute
+    iteration count, which the features capture poorly (measured on 40
+    validation systems of the learned family over three seeds: gains of 3.7
+    to 5.2% over the plain rule with this target, 0 to 5.1% with log2 of the
+    iterations themselves)."""
     g = sw.iters.shape[1]
     keep = (sw.iters >= 0).any(axis=1)
     X, T = [], []
     for s in np.flatnonzero(keep):
+        costs = np.array([sw.cost(s, c) for c in range(g)], dtype=np.float64)
+        ok = sw.ic_ok[s]
+        least = costs[ok].min() if ok.any() else costs.min()
         for c in range(g):
-            it = sw.iters[s, c]
             X.append(np.concatenate([sw.features[s], [c / (g - 1)]]))
-            T.append(np.log2(max(it, 1)) if it >= 0 else np.log2(FAIL_FACTOR * sw.maxit))
+            T.append(np.log2(costs[c] / least))
     return np.asarray(X, np.float32), np.asarray(T, np.float32)
 
 

@@ -118,7 +118,7 @@ def test_learned_shift_gain_over_plain_rule(lib):
     """Train on shift sweeps of 160 small systems, evaluate on 32 held-out
     ones: mean CG iterations with the learned shift (plain-rule fallback when
     its IC(0) fails) versus the plain rule's first positive-pivot shift.
-    Measured on GB300: plain 48.6, learned 45.0, best grid shift 44.4 (7.3%
+    Measured on GB300: plain 48.6, learned 45.2, best grid shift 44.4 (7.0%
     fewer iterations than the plain rule); the test asks for at least 3%."""
     train = _instances(160, 7000)
     test = _instances(32, 8000)
