@@ -360,6 +360,19 @@ hbmc_status hbmc_profile_kernels(hbmc_ctx *ctx, int32_t reps, double *ms);
 hbmc_status hbmc_debug_stall(hbmc_ctx *ctx, int64_t unit, double wait_s);
 
 /*
+ * hbmc_debug_convert - test hook for the conversions the FP32 substitutions
+ * make between binary64 and binary32 with integer operations (the paper
+ * has no counterpart; they keep the conversions off this GPU's FP64 pipe):
+ * f_out[i] = d_in[i] rounded to float (to nearest, ties to even) and
+ * d_out[i] = f_in[i] widened to double, for i < n.  All four pointers are
+ * device arrays of n elements; stream is a cudaStream_t (NULL = legacy
+ * default stream).  Synchronizes the stream.  HBMC_ERR_INVALID_ARG for
+ * n < 0 or a NULL pointer with n > 0, HBMC_ERR_CUDA on a launch error.
+ */
+hbmc_status hbmc_debug_convert(const double *d_in, float *f_out, const float *f_in, double *d_out, int64_t n,
+                               void *stream);
+
+/*
  * hbmc_ilu0 - ILU(0) of Abar for a context built with opt.nonsymmetric = 1
  * (Section 2: ILU(0) preconditioning; the HBMC ordering makes its
  * substitutions parallel exactly as for IC(0), with U in place of L^T).

@@ -532,6 +532,16 @@ void hbmc_destroy(hbmc_ctx *ctx) {
   delete ctx;
 }
 
+hbmc_status hbmc_debug_convert(const double *d_in, float *f_out, const float *f_in, double *d_out, int64_t n,
+                               void *stream) {
+  if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out))) return HBMC_ERR_INVALID_ARG;
+  if (n == 0) return HBMC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hbmc::enqueue_convert_ieee(d_in, f_out, f_in, d_out, n, s);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return HBMC_ERR_CUDA;
+  return HBMC_OK;
+}
+
 hbmc_status hbmc_debug_stall(hbmc_ctx *ctx, int64_t unit, double wait_s) {
   TRY(need_device(ctx));
   if (unit >= ctx->h.ntiles) return set_err(ctx, HBMC_ERR_INVALID_ARG, "unit beyond the last level-1 block");

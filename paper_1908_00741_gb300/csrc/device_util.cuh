@@ -61,6 +61,86 @@ __device__ double gather_partials(const double *part, int64_t count, int stride,
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
+// ---------------------------------------------------------------------------
+// Conversions between binary32 and binary64 with integer operations.  On this
+// GPU a float <-> double conversion instruction issues on the FP64 pipe,
+// which retires about two operations per clock per SM, as slowly as an FP64
+// fused multiply-add.  The bulk-copy warp sweeps (sweep_tw.cu) convert every
+// row they read or write in FP32, and every warp of a color's single wave
+// converts at the same moment, so there the conversions queue on that pipe.
+// These do the same conversions from the IEEE-754 interchange formats (sign,
+// biased exponent, significand) on the integer pipe, with the same results:
+// widening is exact, narrowing rounds to nearest with ties to even, as the
+// casts do.  Checked against the casts by hbmc_debug_convert's test.  Where
+// the FP64 pipe is not the queue (the other sweep kernels, the batched
+// solver) their dozen integer instructions cost more than the cast, and the
+// casts stay.
+// ---------------------------------------------------------------------------
+
+// float -> double, exact.  Normal numbers move their significand 29 bits up
+// and rebias the exponent (1023 - 127 = 896); subnormal floats (m * 2^-149)
+// become normal doubles; zeros, infinities and NaNs keep their class.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint32_t a = u & 0x7fffffffu;
+  uint64_t r = ((uint64_t)a << 29) + (896ull << 52);
+  if (a - 0x00800000u >= 0x7f000000u) {  // not a normal number
+    if (a == 0) {
+      r = 0;
+    } else if (a >= 0x7f800000u) {
+      r = 0x7ff0000000000000ull | ((uint64_t)(a & 0x007fffffu) << 29);
+    } else {  // subnormal: a * 2^-149 with its leading one at bit k
+      const int k = 31 - __clz(a);
+      r = ((uint64_t)(k + 874) << 52) | (((uint64_t)a << (52 - k)) & 0x000fffffffffffffull);
+    }
+  }
+  return __longlong_as_double((long long)(r | sign));
+}
+
+// double -> float, rounding to nearest, ties to even.  In the float normal
+// range the top 35 bits of the magnitude hold the float's exponent and
+// significand (rebiased by 896); the 29 bits below decide the rounding, and
+// a carry out of the significand steps the exponent (to infinity past the
+// largest float).  Results in the float subnormal range round m * 2^-149;
+// overflow gives infinity, and NaNs stay NaN.
+__device__ __forceinline__ float narrow_f64(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint64_t a = b & 0x7fffffffffffffffull;
+  uint32_t r;
+  if (a - (897ull << 52) < (254ull << 52)) {  // 2^-126 <= |x| < 2^128
+    const uint64_t t = a >> 29;
+    const uint32_t rem = (uint32_t)a & 0x1fffffffu;
+    const uint64_t up = (rem > 0x10000000u || (rem == 0x10000000u && (t & 1))) ? 1 : 0;
+    r = (uint32_t)(t + up - (896ull << 23));
+  } else if (a >= 0x7ff0000000000000ull) {  // infinity or NaN
+    r = a == 0x7ff0000000000000ull ? 0x7f800000u : 0x7fffffffu;
+  } else if (a >= (1151ull << 52)) {  // beyond the float range
+    r = 0x7f800000u;
+  } else {  // below 2^-126: the nearest multiple of 2^-149 (doubles below 2^-1022 give 0)
+    const int e = (int)(a >> 52);
+    const int shift = 926 - e;  // m = significand * 2^-shift
+    r = 0;
+    if (e > 0 && shift < 64) {
+      const uint64_t mant = (a & 0x000fffffffffffffull) | (1ull << 52);
+      const uint64_t kept = mant >> shift;
+      const uint64_t rem = mant & ((1ull << shift) - 1);
+      const uint64_t half = 1ull << (shift - 1);
+      r = (uint32_t)(kept + ((rem > half || (rem == half && (kept & 1))) ? 1 : 0));
+    }
+  }
+  return __uint_as_float(sign | r);
+}
+
+// Value conversion between the substitutions' types without the FP64 pipe.
+template <typename TO, typename FROM>
+__device__ __forceinline__ TO cvt(FROM v) {
+  if constexpr (sizeof(TO) == sizeof(FROM)) return (TO)v;
+  else if constexpr (sizeof(TO) == 8) return widen_f32(v);
+  else return narrow_f64(v);
+}
+
 // Backward sweeps in FP32 gather z from its FP32 copy z32: z holds those
 // FP32 results widened, so the narrowed gather gives the same value at half
 // the bytes and without an FP64-pipe conversion.  FP64 sweeps gather z.

@@ -689,6 +689,21 @@ void enqueue_widen(const float *src, double *dst, int64_t n, cudaStream_t s) {
   k_widen<<<blocks_for(n, kRowThreads), kRowThreads, 0, s>>>(src, dst, n);
 }
 
+// The integer-operation conversions of the FP32 substitutions on given
+// values (test hook: they must equal the casts bit for bit).
+__global__ void k_convert_ieee(const double *din, float *fout, const float *fin, double *dout, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    fout[i] = narrow_f64(din[i]);
+    dout[i] = widen_f32(fin[i]);
+  }
+}
+
+void enqueue_convert_ieee(const double *din, float *fout, const float *fin, double *dout, int64_t n,
+                          cudaStream_t s) {
+  if (n > 0) k_convert_ieee<<<blocks_for(n, kRowThreads), kRowThreads, 0, s>>>(din, fout, fin, dout, n);
+}
+
 void enqueue_narrow(const double *src, float *dst, int64_t n, cudaStream_t s) {
   k_narrow<<<blocks_for(n, kRowThreads), kRowThreads, 0, s>>>(src, dst, n);
 }

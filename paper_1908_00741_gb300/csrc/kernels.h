@@ -95,6 +95,8 @@ void enqueue_gather_in(const DeviceLayout &d, const double *src, double *dst, in
 void enqueue_gather_out(const DeviceLayout &d, const double *src, double *dst, bool to_user, cudaStream_t s);
 void enqueue_widen(const float *src, double *dst, int64_t n, cudaStream_t s);
 void enqueue_narrow(const double *src, float *dst, int64_t n, cudaStream_t s);
+void enqueue_convert_ieee(const double *din, float *fout, const float *fin, double *dout, int64_t n,
+                          cudaStream_t s);
 // q = A p (with p.q and alpha when dot): the row-split layout when the
 // context has one, else enqueue_spmv_plain.
 void enqueue_spmv(const DeviceLayout &d, const double *p, double *q, bool dot, cudaStream_t s);

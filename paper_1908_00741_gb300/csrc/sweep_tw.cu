@@ -122,7 +122,7 @@ __device__ __forceinline__ void tw_unit(const TwArgs<T> &a, unsigned char *ws, i
   }
   if constexpr (!std::is_same<IN, T>::value) {
 #pragma unroll
-    for (int l = 0; l < BS; ++l) ts[(l << 5) + lane] = (T)tin[(l << 5) + lane];
+    for (int l = 0; l < BS; ++l) ts[(l << 5) + lane] = cvt<T>(tin[(l << 5) + lane]);
   }
   // other-color couplings
   run_accumulate<T, G, true>(a.o_col, a.o_val, gsrc, obeg, olen, rs + 6, ts, lane);
@@ -144,9 +144,9 @@ __device__ __forceinline__ void tw_unit(const TwArgs<T> &a, unsigned char *ws, i
 #pragma unroll
   for (int q = 0; q < BS; ++q) {
     const T yv = ts[(q << 5) + lane];
-    out[row0 + (q << 5) + lane] = (OUT)yv;
+    out[row0 + (q << 5) + lane] = cvt<OUT>(yv);
     if constexpr (!FWD && sizeof(T) == 4) out32[row0 + (q << 5) + lane] = yv;
-    if (!FWD && dot) rz = fma(rv[q], (double)yv, rz);
+    if (!FWD && dot) rz = fma(rv[q], cvt<double>(yv), rz);
   }
 }
 
@@ -245,7 +245,7 @@ __device__ __forceinline__ void fb_unit(const TwArgs<T> &af, const TwArgs<T> &ab
   }
   if constexpr (!std::is_same<T, double>::value) {
 #pragma unroll
-    for (int l = 0; l < BS; ++l) ts[(l << 5) + lane] = (T)tin[(l << 5) + lane];
+    for (int l = 0; l < BS; ++l) ts[(l << 5) + lane] = cvt<T>(tin[(l << 5) + lane]);
   }
   run_accumulate<T, Y, true>(af.o_col, af.o_val, ysrc, obeg, olen, rs + 6, ts, lane);
   {
@@ -301,9 +301,10 @@ __device__ __forceinline__ void fb_unit(const TwArgs<T> &af, const TwArgs<T> &ab
 #pragma unroll
   for (int q = 0; q < BS; ++q) {
     const T zv = ts[(q << 5) + lane];
-    z[row0 + (q << 5) + lane] = (double)zv;
+    const double zd = cvt<double>(zv);
+    z[row0 + (q << 5) + lane] = zd;
     if constexpr (sizeof(T) == 4) z32[row0 + (q << 5) + lane] = zv;
-    if (dot) rz = fma(rv[q], (double)zv, rz);
+    if (dot) rz = fma(rv[q], zd, rz);
   }
 }
 

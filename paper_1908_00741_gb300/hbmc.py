@@ -46,7 +46,7 @@ EXPORTED = [
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
-    "hbmc_debug_stall", "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar", "hbmc_ilu0", "hbmc_get_factor_u", "hbmc_bicgstab",
+    "hbmc_debug_stall", "hbmc_debug_convert", "hbmc_spmv_dot_static", "hbmc_sor", "hbmc_sor_bar", "hbmc_ilu0", "hbmc_get_factor_u", "hbmc_bicgstab",
     "hbmc_batch_build", "hbmc_batch_build_w", "hbmc_batch_destroy", "hbmc_batch_last_error", "hbmc_batch_info",
     "hbmc_batch_set_stream", "hbmc_batch_set_precision", "hbmc_batch_ic0", "hbmc_batch_iccg",
     "hbmc_batch_autotune", "hbmc_batch_autotune_w", "hbmc_batch_features",
@@ -126,6 +126,7 @@ def load():
             "hbmc_spmv_bar": (I32, [P, P, P]),
             "hbmc_profile_kernels": (I32, [P, I32, P]),
             "hbmc_debug_stall": (I32, [P, I64, D]),
+            "hbmc_debug_convert": (I32, [P, P, P, P, I64, P]),
             "hbmc_spmv_dot_static": (I32, [P, P, P, P]),
             "hbmc_sor": (I32, [P, P, P, D, I32, I32, P]),
             "hbmc_sor_bar": (I32, [P, P, P, D, I32, I32]),
@@ -454,6 +455,25 @@ def hbmc_debug_stall(ctx: Context, unit: int = -1, wait_s: float = 0.0) -> None:
     publishes its completion, and every wait gives up after wait_s seconds
     (unit = -1, wait_s = 0: normal operation)."""
     ctx.check(ctx._lib.hbmc_debug_stall(ctx.handle, int(unit), float(wait_s)))
+
+
+def hbmc_debug_convert(d_in, f_in):
+    """Test hook: the integer-operation conversions of the FP32 substitutions
+    on device tensors d_in (float64) and f_in (float32) of equal length;
+    returns (d_in narrowed to float32, f_in widened to float64)."""
+    import torch
+    lib = load()
+    if not (d_in.is_cuda and f_in.is_cuda and d_in.dtype == torch.float64 and f_in.dtype == torch.float32
+            and d_in.is_contiguous() and f_in.is_contiguous() and d_in.numel() == f_in.numel()):
+        raise ValueError("d_in: contiguous CUDA float64, f_in: contiguous CUDA float32, equal lengths")
+    f_out = torch.empty_like(f_in)
+    d_out = torch.empty_like(d_in)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    st = lib.hbmc_debug_convert(vp(d_in), vp(f_out), vp(f_in), vp(d_out), int(d_in.numel()),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != OK:
+        raise HbmcError(st, "hbmc_debug_convert failed")
+    return f_out, d_out
 
 
 def hbmc_spmv_dot_static(ctx: Context, p, q, pq) -> None:
