@@ -121,6 +121,8 @@ def test_sequential_dot_within_bound_of_exact(orc, a, seed):
     # of sum |a_i b_i|, plus, where products or partial sums fall below the
     # normal range, an absolute error of at most half the smallest subnormal
     # (2^-1075) per rounding, 2k roundings
+    # (2^-1075 as an exact rational: the float literal 2.0 ** -1075 is half
+    # the smallest subnormal and rounds to zero)
     bound = fractions.Fraction(k * u / (1 - k * u)) * sum(abs(fractions.Fraction(float(x)) * fractions.Fraction(float(y)))
-                                                         for x, y in zip(a, b)) + 2 * k * fractions.Fraction(2.0 ** -1075)
+                                                         for x, y in zip(a, b)) + 2 * k * fractions.Fraction(1, 2 ** 1075)
     assert abs(fractions.Fraction(seq) - true) <= bound
