@@ -133,13 +133,18 @@ def test_dag_graph_and_host_loop_agree_bitwise(lib):
         np.testing.assert_array_equal(x, xs[0][1])
 
 
-@pytest.mark.parametrize("m,loop_mode", [(10, H.LOOP_GRAPH), (10, H.LOOP_HOST), (60, H.LOOP_GRAPH)])
-def test_dag_wait_runs_out_and_context_recovers(lib, m, loop_mode):
-    """A level-1 block of the first color withholds its completion: the
-    level-1 blocks of later colors that gather from it (through its flag at
-    10^3, through its color's counter at 60^3) wait 0.2 s, give up, and the
-    solve returns HBMC_ERR_TIMEOUT.  With the hook cleared the same context
-    solves again, to the same bits as an undisturbed context."""
+@pytest.mark.parametrize("m,loop_mode,last", [(10, H.LOOP_GRAPH, False), (10, H.LOOP_HOST, False),
+                                               (60, H.LOOP_GRAPH, False), (60, H.LOOP_GRAPH, True),
+                                               (60, H.LOOP_HOST, True)])
+def test_dag_wait_runs_out_and_context_recovers(lib, m, loop_mode, last):
+    """A level-1 block withholds its completion: the level-1 blocks that
+    gather from it (through its flag at 10^3, through its color's counter at
+    60^3) wait 0.2 s, give up, and the solve returns HBMC_ERR_TIMEOUT.  A
+    block of the first color stalls the forward sweep; a block of the last
+    color (last = True) is read by nobody in the forward sweep, so the wait
+    runs out in the backward sweep, the one that reduces r.z.  With the hook
+    cleared the same context solves again, to the same bits as an
+    undisturbed context (the reduction counters start clean)."""
     A = W.permute_input(W.heterogeneous_stencil(m, 27, 2.0, 1), W.random_order(2, m ** 3))
     b, _ = W.rhs_from_solution(A, 0)
     ref_ctx = H.hbmc_build(A, 8, 32, sweep_kernel=8)
@@ -150,7 +155,7 @@ def test_dag_wait_runs_out_and_context_recovers(lib, m, loop_mode):
     ctx = H.hbmc_build(A, 8, 32, sweep_kernel=8, loop_mode=loop_mode)
     assert H.hbmc_ic0(ctx)[0] == H.OK
     assert ctx.info()["nc"] > 2
-    H.hbmc_debug_stall(ctx, 0, 0.2)
+    H.hbmc_debug_stall(ctx, ctx.info()["ntiles"] - 1 if last else 0, 0.2)
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     with pytest.raises(H.HbmcError) as e:
         H.hbmc_iccg(ctx, dev(b), x)
