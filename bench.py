@@ -406,7 +406,7 @@ def run_gpu(args):
         "dtype": args.precision, "data": "synthetic",
         "config": {"workload": f"7-point Poisson {GRID}^3 ({A.n} unknowns, {A.nnz} nonzeros), "
                                f"bs={bs} ({'x'.join(map(str, P.box))} boxes), w=32, "
-                               f"{args.precision.upper()} substitutions, tol {TOL:g}",
+                               f"FP{args.precision[1:]} substitutions, tol {TOL:g}",
                    "n": A.n, "nnz": A.nnz, "bs": bs, "w": 32, "colors": inf["nc"],
                    "precision": args.precision, "parallelism": f"replicas{world}", "loop": args.loop,
                    "l2": "inputs larger than L2 (device working set "
