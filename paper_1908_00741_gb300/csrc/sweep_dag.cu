@@ -87,6 +87,7 @@ struct DagArgs {
   int64_t units;
   int nc;
   int64_t stall;     // test hook: this level-1 block never publishes (-1: none)
+  int64_t lookahead; // tickets between a CUDA block and the one whose operands it prefetches into L2
   uint64_t wait_ns;  // bound of every wait
   int rec_ints, bs, x_stride;
   uint32_t off_xr, off_ts, off_tin, off_ds, off_rr, off_oc, off_vv, off_iv, off_im, off_pos;
@@ -293,6 +294,21 @@ __device__ __forceinline__ int64_t dag_unit(const DagArgs<T> &a, unsigned char *
   const int ilen = rs[1];
   const int64_t ibeg = rec64(rs, 4), xbeg = s_x[0];
   const uint32_t xlen = (uint32_t)(s_x[1] - s_x[0]);  // a multiple of 32 entries
+  // The level-1 block one resident set of CUDA blocks later in the sweep
+  // will get its slot when some block ahead of it leaves, typically as the
+  // color before it completes, with its copies on the critical path: its
+  // contiguous operands go to L2 now (a thread that is otherwise waiting).
+  if (tid == 32 && k + a.lookahead < a.units) {
+    const int64_t k2 = k + a.lookahead;
+    const int64_t u2 = a.order ? (int64_t)a.order[k2] : k2;
+    prefetch_l2(in + u2 * (int64_t)R, R * (uint32_t)sizeof(IN));
+    prefetch_l2(a.dinv + u2 * (int64_t)R, R * (uint32_t)sizeof(T));
+    const int64_t xb = a.x_ptr[u2], xe = a.x_ptr[u2 + 1];
+    if (xe > xb) {
+      prefetch_l2(a.x_col + xb, (uint32_t)(xe - xb) * 4u);
+      prefetch_l2(a.x_val + xb, (uint32_t)(xe - xb) * (uint32_t)sizeof(T));
+    }
+  }
   if (tid == 0) {
     mbar_arrive_expect_tx(bar, xlen * (uint32_t)(4 + sizeof(T)) + (uint32_t)ilen * (uint32_t)(1 + sizeof(T)));
     if (xlen > 0) {
@@ -503,6 +519,7 @@ DagArgs<T> dag_args(const DeviceLayout &d, bool fwd, const DagPlan &p) {
   a.abort = d.dag_abort + (fwd ? 0 : 1);
   a.units = d.nc > 0 ? d.tile_ptr[d.nc] : 0;
   a.stall = d.dag_stall;
+  a.lookahead = (int64_t)d.sm_count * kDagMinBlocks;
   a.wait_ns = d.dag_wait_ns;
   a.bs = d.bs;
   a.off_xr = p.off_xr;
