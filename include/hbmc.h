@@ -455,8 +455,9 @@ hbmc_status hbmc_sor_bar(hbmc_ctx *ctx, const double *b_dev, double *x_dev, doub
  * blocks (n_pad <= 32768 * bs * 32); larger contexts get
  * HBMC_ERR_INVALID_ARG with the limit in hbmc_last_error.  Calls no
  * cudaMalloc or cudaFree.  The first call on a device looks up the static
- * array's device address and sets a kernel attribute.  All calls on a device
- * share the array: each clears it on its own stream before use, and calls whose
+ * array's device address and sets a kernel attribute, so make that first
+ * call before any stream capture begins.  All calls on a device share the
+ * array: each clears it on its own stream before use, and calls whose
  * kernels could overlap on the GPU race, so order them (one stream, or
  * events).
  */
