@@ -257,6 +257,7 @@ hbmc_status upload(hbmc_ctx *ctx) {
       TRY(dalloc(ctx, d.dag_ticket, 2));
       hbmc::plan_dag_kernels(h, d);
       CK(hbmc::setup_dag_kernels());
+      CK(hbmc::dag_occupancy(d));
     }
   }
   hbmc::plan_sor(h, d);

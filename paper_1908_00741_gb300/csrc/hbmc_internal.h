@@ -186,10 +186,12 @@ struct WidePlan {
 };
 
 // Shared memory of the dependency-driven sweeps (sweep_dag.cu), byte
-// offsets; ok = false when a level-1 block's runs do not fit.
+// offsets; ok = false when a level-1 block's runs do not fit.  resident:
+// CUDA blocks of the launch that fit on one SM (registers and shared memory).
 struct DagPlan {
   uint32_t off_xr = 0, off_ts = 0, off_tin = 0, off_ds = 0, off_rr = 0, off_oc = 0, off_vv = 0, off_iv = 0,
            off_im = 0, off_pos = 0, smem_bytes = 0;
+  int resident = 0;
   bool ok = false;
 };
 

@@ -62,6 +62,7 @@ struct DagTables {
 bool dag_host_tables(const HostLayout &h, DagTables &t);
 void plan_dag_kernels(const HostLayout &h, DeviceLayout &d);
 cudaError_t setup_dag_kernels();
+cudaError_t dag_occupancy(DeviceLayout &d);
 bool dag_usable(const DeviceLayout &d, bool fwd, int prec);
 bool dag_selected(const DeviceLayout &d, int prec);
 void enqueue_fwd_dag(const DeviceLayout &d, int prec, const double *r, bool check_done, cudaStream_t s);

@@ -58,7 +58,14 @@ constexpr int kDagGather = 16;         // gathers in flight per thread
 constexpr int64_t kDagColorWait = 16;
 constexpr int kDagChain = 4;  // same-block terms loaded together in a chain step
 constexpr unsigned kDagPollCheck = 64;  // polls between looks at the abort word and the clock
-constexpr int kDagMinBlocks = 3;
+// CUDA blocks per SM the register allocation leaves room for: 3 at up to 85
+// registers a thread, 4 at up to 64.  The FP32 kernels fit 64 without
+// spilling; the FP64 backward sweep would spill, so it keeps 3.  Shared
+// memory may hold a launch to fewer (dag_occupancy).
+template <typename T>
+constexpr int dag_min_blocks() {
+  return sizeof(T) == 4 ? 4 : 3;
+}
 constexpr int kDagAutoColors = 8;               // automatic selection: at least this many colors
 constexpr uint32_t kDagAutoSmem = 110 * 1024;   // ... and two CUDA blocks per SM
 
@@ -431,7 +438,7 @@ __device__ __forceinline__ void dag_exit(const DagArgs<T> &a) {
 }
 
 template <typename T, typename Y, int BS>
-__global__ void __launch_bounds__(kDagThreads, kDagMinBlocks)
+__global__ void __launch_bounds__(kDagThreads, dag_min_blocks<T>())
     k_fwd_dag(const DagArgs<T> a, const double *__restrict__ r, Y *y, Scalars *sc, int check_done) {
   extern __shared__ __align__(128) unsigned char smem[];
   double rz = 0.0;
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(kDagThreads, kDagMinBlocks)
 }
 
 template <typename T, typename Y, int BS>
-__global__ void __launch_bounds__(kDagThreads, kDagMinBlocks)
+__global__ void __launch_bounds__(kDagThreads, dag_min_blocks<T>())
     k_bwd_dag(const DagArgs<T> a, const Y *__restrict__ yin, double *z, float *z32, const double *__restrict__ r,
               Scalars *sc, int check_done, int dot_mode, double *part) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -519,7 +526,7 @@ DagArgs<T> dag_args(const DeviceLayout &d, bool fwd, const DagPlan &p) {
   a.abort = d.dag_abort + (fwd ? 0 : 1);
   a.units = d.nc > 0 ? d.tile_ptr[d.nc] : 0;
   a.stall = d.dag_stall;
-  a.lookahead = (int64_t)d.sm_count * kDagMinBlocks;
+  a.lookahead = (int64_t)d.sm_count * std::max(p.resident, 1);
   a.wait_ns = d.dag_wait_ns;
   a.bs = d.bs;
   a.off_xr = p.off_xr;
@@ -635,6 +642,29 @@ cudaError_t setup_dag_kernels() {
   cudaError_t e;
   if ((e = allow_bs<0>()) || (e = allow_bs<4>()) || (e = allow_bs<8>())) return e;
   return cudaSuccess;
+}
+
+template <int BS>
+static cudaError_t occupancy_bs(DeviceLayout &d) {
+  DagPlan *plans[4] = {&d.dg_f64_f, &d.dg_f64_b, &d.dg_f32_f, &d.dg_f32_b};
+  const void *kernels[4] = {(const void *)k_fwd_dag<double, double, BS>, (const void *)k_bwd_dag<double, double, BS>,
+                            (const void *)k_fwd_dag<float, float, BS>, (const void *)k_bwd_dag<float, float, BS>};
+  for (int i = 0; i < 4; ++i) {
+    plans[i]->resident = 0;
+    if (!plans[i]->ok) continue;
+    int blocks = 0;
+    const cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernels[i], kDagThreads, plans[i]->smem_bytes);
+    if (e != cudaSuccess) return e;
+    plans[i]->resident = blocks;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t dag_occupancy(DeviceLayout &d) {
+  if (d.bs == 8) return occupancy_bs<8>(d);
+  if (d.bs == 4) return occupancy_bs<4>(d);
+  return occupancy_bs<0>(d);
 }
 
 bool dag_usable(const DeviceLayout &d, bool fwd, int prec) {
