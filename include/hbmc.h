@@ -241,6 +241,29 @@ hbmc_status hbmc_get_split(const hbmc_ctx *ctx, int32_t *head);
  */
 hbmc_status hbmc_get_vslice(const hbmc_ctx *ctx, int32_t *height);
 
+/*
+ * hbmc_get_dag_deps - what each level-1 block of a dependency-driven sweep
+ * (sweep_kernel 8, chosen automatically for 8 or more colors) waits for.
+ * Section 4.3.3 counts n_c - 1 barriers per substitution; these sweeps
+ * replace them by waits on only the level-1 blocks whose rows a level-1
+ * block reads through its other-color couplings (Eq. "for3").
+ *
+ * dir: 0 forward sweep (entries of earlier colors), 1 backward sweep (later
+ * colors).  ptr: int64[ntiles + 1], level-1 block u's entries are
+ * dep[ptr[u] .. ptr[u + 1]).  An entry v >= 0 is a level-1 block (index into
+ * the level-1 blocks of all colors, colors in order); an entry -(c + 1) is
+ * color c, whose completion counter replaces the level-1 blocks of that
+ * color where u reads more than 16 of them.  Entries are sorted by the first
+ * row they cover (forward) or by the row after their last, descending
+ * (backward), the order in which the sweep gathers their terms.  dep:
+ * int32[cap], may be NULL to query *count (the total number of entries)
+ * first; ptr and count may be NULL too.  Works for host_only contexts.
+ * INVALID_ARG when w != 32, the context has no level-1 block, dir is not 0
+ * or 1, or dep is given with cap < *count (*count is still set).
+ */
+hbmc_status hbmc_get_dag_deps(const hbmc_ctx *ctx, int32_t dir, int64_t *ptr, int32_t *dep, int64_t cap,
+                              int64_t *count);
+
 /* Bind the context to a CUDA stream (a cudaStream_t, e.g. from
  * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */
 hbmc_status hbmc_set_stream(hbmc_ctx *ctx, void *stream);

@@ -610,6 +610,28 @@ hbmc_status hbmc_get_vslice(const hbmc_ctx *ctx, int32_t *height) {
   return HBMC_OK;
 }
 
+hbmc_status hbmc_get_dag_deps(const hbmc_ctx *ctx, int32_t dir, int64_t *ptr, int32_t *dep, int64_t cap,
+                              int64_t *count) {
+  if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
+  if (dir != 0 && dir != 1) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "dir must be 0 (forward) or 1 (backward)");
+  hbmc::DagTables t;
+  try {
+    if (!hbmc::dag_host_tables(ctx->h, t))
+      return set_err(nullptr, HBMC_ERR_INVALID_ARG,
+                     "the dependency-driven sweeps need w = 32 and at least one level-1 block");
+  } catch (const std::bad_alloc &) {
+    return set_err(nullptr, HBMC_ERR_OOM, "host allocation failed");
+  }
+  const std::vector<int64_t> &p = dir == 0 ? t.ptr_f : t.ptr_b;
+  const std::vector<int32_t> &v = dir == 0 ? t.dep_f : t.dep_b;
+  if (count) *count = (int64_t)v.size();
+  if (dep && cap < (int64_t)v.size())
+    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "cap is smaller than the number of entries");
+  if (ptr) std::memcpy(ptr, p.data(), sizeof(int64_t) * p.size());
+  if (dep && !v.empty()) std::memcpy(dep, v.data(), sizeof(int32_t) * v.size());
+  return HBMC_OK;
+}
+
 hbmc_status hbmc_get_ordering(const hbmc_ctx *ctx, int64_t *pi, int64_t *color_ptr, int64_t *block_of,
                               int32_t *block_color) {
   if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");

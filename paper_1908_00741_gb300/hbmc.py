@@ -43,6 +43,7 @@ LOOP_PERSISTENT = 2
 EXPORTED = [
     "hbmc_default_options", "hbmc_build", "hbmc_destroy", "hbmc_last_error",
     "hbmc_status_string", "hbmc_info", "hbmc_get_ordering", "hbmc_get_matrix", "hbmc_get_split", "hbmc_get_vslice",
+    "hbmc_get_dag_deps",
     "hbmc_set_stream", "hbmc_set_precision", "hbmc_ic0", "hbmc_get_factor",
     "hbmc_precond", "hbmc_iccg", "hbmc_iccg_host", "hbmc_residual_history",
     "hbmc_fwd_bar", "hbmc_bwd_bar", "hbmc_spmv_bar", "hbmc_profile_kernels",
@@ -113,6 +114,7 @@ def load():
             "hbmc_get_matrix": (I32, [P, P, P, P]),
             "hbmc_get_split": (I32, [P, P]),
             "hbmc_get_vslice": (I32, [P, P]),
+            "hbmc_get_dag_deps": (I32, [P, I32, P, P, I64, P]),
             "hbmc_set_stream": (I32, [P, P]),
             "hbmc_set_precision": (I32, [P, I32]),
             "hbmc_ic0": (I32, [P, D, P]),
@@ -317,6 +319,20 @@ def hbmc_get_vslice(ctx: Context):
     h = np.empty(max(inf["n_pad"] // max(inf["w"], 1), 1), dtype=np.int32)
     ctx.check(ctx._lib.hbmc_get_vslice(ctx.handle, _np_ptr(h)))
     return h[: inf["n_pad"] // max(inf["w"], 1)]
+
+
+def hbmc_get_dag_deps(ctx: Context, direction: int):
+    """What each level-1 block of the dependency-driven forward (0) or
+    backward (1) sweep waits for: (ptr[ntiles + 1], dep[count]); entries >= 0
+    are level-1 blocks, -(c + 1) the completion counter of color c."""
+    count = ctypes.c_int64(0)
+    ctx.check(ctx._lib.hbmc_get_dag_deps(ctx.handle, direction, None, None, 0, ctypes.byref(count)))
+    inf = ctx.info()
+    ptr = np.empty(inf["ntiles"] + 1, dtype=np.int64)
+    dep = np.empty(max(count.value, 1), dtype=np.int32)
+    ctx.check(ctx._lib.hbmc_get_dag_deps(ctx.handle, direction, _np_ptr(ptr), _np_ptr(dep), count.value,
+                                         ctypes.byref(count)))
+    return ptr, dep[: count.value]
 
 
 def hbmc_set_stream(ctx: Context, stream) -> None:
