@@ -606,8 +606,16 @@ typedef struct hbmc_mlp hbmc_mlp; /* device-resident network and optimizer state
 /* Number of parameters for input width in_dim (layout: W1[32][D], b1[32],
  * W2[32][32], b2[32], w3[32], b3). */
 int32_t hbmc_mlp_num_params(int32_t in_dim);
+/* A network of in_dim inputs (1..256) on the current device, parameters all
+ * zero, input standardization mean 0 and std 1 (set real ones with
+ * hbmc_mlp_set_params).  *out receives it; the caller frees it with
+ * hbmc_mlp_destroy.  INVALID_ARG for a bad in_dim or a NULL out, OOM when the
+ * device memory cannot be had (then *out is NULL). */
 hbmc_status hbmc_mlp_create(int32_t in_dim, hbmc_mlp **out);
+/* Frees the network and its device memory; NULL is ignored. */
 void hbmc_mlp_destroy(hbmc_mlp *net);
+/* Message of the last failed call on net (NULL: of the last failed
+ * hbmc_mlp_create). */
 const char *hbmc_mlp_last_error(const hbmc_mlp *net);
 /* Host parameters (NULL keeps the current ones) and input standardization
  * (mean, std > 0; NULL keeps them); resets the optimizer state. */
