@@ -202,3 +202,48 @@ def test_checker_catches_planted_mistakes(lib):
                 _check_direction(p, d, rp, ci, R, tile_color, tile_ptr, True)
     finally:
         ctx.close()
+
+
+def _random_spd(n, density, seed, hubs):
+    """A random symmetric pattern with a few dense rows and a strictly
+    dominant diagonal (CSR, sorted columns)."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    M = sp.random(n, n, density=density, random_state=seed).tolil()
+    for h in rng.choice(n, size=min(n, hubs), replace=False):
+        M[h, rng.choice(n, size=max(1, n // 3), replace=False)] = 1.0
+    S = (M + M.T).tocsr()
+    S.setdiag(0.0)
+    S.eliminate_zeros()
+    S.data = -np.abs(S.data) - 0.1
+    S = (S + sp.identity(n) * (abs(S).sum(axis=1).max() + 1.0)).tocsr()
+    S.sort_indices()
+    return W.CSR(n, S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data.astype(np.float64))
+
+
+def test_dag_wait_lists_random_patterns(lib):
+    """The same checks over random sparse patterns with dense rows, random
+    block sizes and algebraic blocking."""
+    pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, strategies as st
+
+    @settings(max_examples=30, deadline=None)
+    @given(st.integers(1, 900), st.floats(0.0, 0.03), st.integers(0, 2**31 - 1), st.integers(0, 4),
+           st.sampled_from([1, 2, 3, 4, 8]))
+    def check(n, density, seed, hubs, bs):
+        A = _random_spd(n, density, seed, hubs)
+        ctx = H.hbmc_build(A, bs, 32, host_only=True)
+        try:
+            inf = ctx.info()
+            R = bs * 32
+            rp, ci, _ = H.hbmc_get_matrix(ctx)
+            _, color_ptr, _, _ = H.hbmc_get_ordering(ctx)
+            tile_ptr = color_ptr // R
+            tile_color = np.repeat(np.arange(inf["nc"]), np.diff(tile_ptr))
+            for direction, fwd in ((0, True), (1, False)):
+                ptr, dep = H.hbmc_get_dag_deps(ctx, direction)
+                _check_direction(ptr, dep, rp, ci, R, tile_color, tile_ptr, fwd)
+        finally:
+            ctx.close()
+
+    check()
