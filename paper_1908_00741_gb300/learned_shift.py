@@ -66,6 +66,17 @@ def plain_choice(ic_row):
     return int(ok[0]) if len(ok) else -1
 
 
+def fallback_choice(ic_row, c, plain):
+    """The shift actually used when the network chooses grid index c: c if
+    its IC(0) works, else the first larger grid shift whose IC(0) works (as
+    hbmc_ic0_auto continues), else the plain rule's index.  Returns (index,
+    whether the fallback was taken)."""
+    if ic_row[c]:
+        return int(c), False
+    nxt = np.flatnonzero(ic_row[c + 1:])
+    return (int(c + 1 + nxt[0]) if len(nxt) else int(plain)), True
+
+
 def best_choice(sw: Sweep, s):
     """argmin of the cost over the shifts whose IC(0) works, ties to the
     smaller shift; -1 if none works."""
@@ -161,11 +172,7 @@ def evaluate(net: H.Mlp, sw: Sweep):
         pc = plain_choice(sw.ic_ok[s])
         if pc < 0:
             continue
-        lc = int(choice[s])
-        fb = not sw.ic_ok[s, lc]
-        if fb:
-            nxt = [c for c in range(lc + 1, sw.ic_ok.shape[1]) if sw.ic_ok[s, c]]
-            lc = nxt[0] if nxt else pc
+        lc, fb = fallback_choice(sw.ic_ok[s], int(choice[s]), pc)
         plain.append(sw.cost(s, pc))
         learned.append(sw.cost(s, lc))
         best.append(sw.cost(s, best_choice(sw, s)))
