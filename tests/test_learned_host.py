@@ -75,3 +75,19 @@ def test_dataset_least_cost_among_factoring_shifts():
 ])
 def test_fallback_choice(ic, c, plain, expect):
     assert LS.fallback_choice(np.array(ic), c, plain) == expect
+
+
+def test_evaluate_with_given_choices(monkeypatch):
+    """evaluate() with the network's choices given: the plain, learned (with
+    fallback) and best costs per system whose IC(0) works somewhere."""
+    sw = _sweep([[-1, 30, 20, 25], [50, 40, 45, 60], [-1, -1, -1, -1], [-1, -1, 35, 30]],
+                [[False, True, True, True], [True, True, True, True], [False, False, False, False],
+                 [False, False, True, True]], maxit=100)
+    choice = np.array([0, 2, 1, 1])
+    monkeypatch.setattr(LS, "predicted_choice", lambda net, feats: (choice, None))
+    plain, learned, best, fallback = LS.evaluate(None, sw)
+    # system 2 factors at no shift and is left out
+    np.testing.assert_array_equal(plain, [30, 50, 35])
+    np.testing.assert_array_equal(learned, [30, 45, 35])   # 0 -> 1 (fallback), 2, 1 -> 2 (fallback)
+    np.testing.assert_array_equal(best, [20, 40, 30])
+    np.testing.assert_array_equal(fallback, [True, False, True])
