@@ -51,3 +51,31 @@ def test_poisson128_iteration_bytes():
 def test_fractions():
     f = bench.fracs(4000.0, 5000.0)
     assert f == {"frac": 0.8, "frac_nominal": 0.5}
+
+
+def test_clock_summary_from_sampled_lines():
+    """The clocks key: median SM clock under load, the highest max clock, and
+    every throttle reason seen active in any sample."""
+    cs = bench.ClockSampler(0)
+    cs.lines = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1950, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+        "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    assert cs.summary() == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    cs.lines.append("0, 1200, 2070, 700.0, 0x48, Active, Not Active, Active, Not Active")
+    assert cs.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                                               "samples": 0}
+
+
+def test_spmv_traffic_record_matches_the_kernel_source():
+    """The ncu traffic the bench reports belongs to the SpMV kernel as it is
+    now: the committed record names the sha1 of its source, and a changed
+    source turns the figure into null."""
+    t = bench.measured_traffic()
+    assert t is not None and t > 0
+    n, nnz = CONFIGS["poisson7_128"]
+    assert 1.0 <= t / bench.spmv_bytes(n, nnz) < 1.1
