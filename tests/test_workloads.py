@@ -64,3 +64,90 @@ def test_splitmix64_reference_values():
     assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
     u = W.uniform(0, 1000)
     assert u.min() >= 0 and u.max() < 1 and abs(u.mean() - 0.5) < 0.05
+
+
+def _edge_gradient(m):
+    """Discrete gradient of a node potential on the m^3 cell grid, in
+    curl_curl's edge numbering (x-, then y-, then z-edges, lexicographic)."""
+    n1 = m + 1
+    node = lambda i, j, k: i + n1 * (j + n1 * k)  # noqa: E731
+    rows, cols, vals = [], [], []
+    e = 0
+    for (di, dj, dk), (ni, nj, nk) in (((1, 0, 0), (m, n1, n1)), ((0, 1, 0), (n1, m, n1)), ((0, 0, 1), (n1, n1, m))):
+        for k in range(nk):
+            for j in range(nj):
+                for i in range(ni):
+                    rows += [e, e]
+                    cols += [node(i + di, j + dj, k + dk), node(i, j, k)]
+                    vals += [1.0, -1.0]
+                    e += 1
+    G = np.zeros((e, n1 ** 3))
+    G[rows, cols] = vals
+    return G
+
+
+@pytest.mark.parametrize("hetero", [0.0, 0.7])
+def test_curl_curl_gradients_are_its_null_space(hetero):
+    """The curl of a gradient is zero, so A = C^T W C + sigma I maps every
+    gradient field g to sigma g: sigma is an eigenvalue of multiplicity
+    (m+1)^3 - 1 (potentials up to a constant), and every other eigenvalue is
+    larger.  A wrong sign on any face of the discrete curl breaks this."""
+    m, sigma = 3, 0.01
+    A = W.curl_curl(m, sigma, 6, hetero)
+    assert A.n == 3 * m * (m + 1) ** 2
+    assert _sym_ok(A)
+    S = A.to_scipy().toarray()
+    G = _edge_gradient(m)
+    phi = np.random.default_rng(0).standard_normal(G.shape[1])
+    g = G @ phi
+    np.testing.assert_allclose(S @ g, sigma * g, atol=1e-12 * np.abs(S).max() * np.abs(g).max())
+    ev = np.linalg.eigvalsh(S)
+    at_sigma = np.abs(ev - sigma) < 1e-9
+    assert at_sigma.sum() == (m + 1) ** 3 - 1
+    assert ev[~at_sigma].min() > sigma + 1e-3
+    # off-diagonal entries of both signs: not an M-matrix
+    off = S[~np.eye(A.n, dtype=bool)]
+    assert (off > 0).any() and (off < 0).any()
+
+
+def test_convection_diffusion_consistency():
+    """Upwind differences are exact on linear functions: on interior rows A
+    annihilates constants and maps the coordinate x_d to c_d.  The pattern is
+    symmetric, the values are not, and A is a diagonally dominant M-matrix."""
+    m, c = 5, (0.5, 0.3, 0.2)
+    A = W.convection_diffusion(m, c)
+    S = A.to_scipy().tocsr()
+    idx = np.arange(m ** 3)
+    x, y, z = idx % m, (idx // m) % m, idx // (m * m)
+    interior = (x > 0) & (x < m - 1) & (y > 0) & (y < m - 1) & (z > 0) & (z < m - 1)
+    np.testing.assert_allclose((S @ np.ones(m ** 3))[interior], 0.0, atol=1e-13)
+    for d, coord in enumerate((x, y, z)):
+        np.testing.assert_allclose((S @ coord.astype(float))[interior], c[d], rtol=1e-13)
+    assert (abs(S - S.T) > 0).nnz > 0
+    assert ((S != 0).astype(int) - (S.T != 0).astype(int)).nnz == 0
+    d = S.diagonal()
+    off = S - np.diag(d)
+    assert off.max() <= 0
+    assert np.all(d >= np.asarray(abs(off).sum(axis=1)).ravel())
+
+
+def test_irregular_structural_translations():
+    """A = sum_e (e_u - e_v)(e_u - e_v)^T (x) S_e plus SPD blocks on boundary
+    nodes: a rigid translation of all nodes is felt only at the boundary, so
+    interior nodes' rows annihilate it; A is symmetric positive definite."""
+    m = 6
+    A = W.irregular_structural(m, 7)
+    assert A.n == 3 * m ** 3
+    assert _sym_ok(A)
+    S = A.to_scipy().toarray()
+    node = np.arange(m ** 3)
+    x, y, z = node % m, (node // m) % m, node // (m * m)
+    inner = (x > 0) & (x < m - 1) & (y > 0) & (y < m - 1) & (z > 0) & (z < m - 1)
+    rows = (3 * node[inner][:, None] + np.arange(3)).ravel()
+    for t in np.eye(3):
+        np.testing.assert_allclose((S @ np.tile(t, m ** 3))[rows], 0.0, atol=1e-12 * np.abs(S).max())
+    assert np.linalg.eigvalsh(S).min() > 0
+    # with a dominance factor every diagonal entry is that factor times its row's off-diagonal sum
+    B = W.irregular_structural(m, 7, dominance=1.1).to_scipy().toarray()
+    offsum = np.abs(B).sum(axis=1) - np.abs(np.diag(B))
+    np.testing.assert_allclose(np.diag(B), 1.1 * offsum, rtol=1e-13)
