@@ -151,3 +151,36 @@ def test_irregular_structural_translations():
     B = W.irregular_structural(m, 7, dominance=1.1).to_scipy().toarray()
     offsum = np.abs(B).sum(axis=1) - np.abs(np.diag(B))
     np.testing.assert_allclose(np.diag(B), 1.1 * offsum, rtol=1e-13)
+
+
+def test_hetero27_dirichlet_surplus():
+    """a_ij = -(k_i + k_j)/2 between neighbouring cells, and the diagonal sums
+    (k_i + k_j)/2 over all 26 neighbour slots with k_j = k_i outside the
+    domain.  k_i is recovered from the matrix itself (three mutually adjacent
+    cells i, j, l give k_i = -a_ij - a_il + a_jl), and each row's diagonal
+    exceeds its off-diagonal sum by exactly k_i per slot outside the domain."""
+    m = 5
+    A = W.heterogeneous_stencil(m, 27, 2.0, 1)
+    S = A.to_scipy().toarray()
+    n = m ** 3
+    idx = np.arange(n)
+    x, y, z = idx % m, (idx // m) % m, idx // (m * m)
+    sx = np.where(x < m - 1, 1, -1)  # a neighbour inside the domain along x, and along y
+    sy = np.where(y < m - 1, 1, -1)
+    j = idx + sx
+    l_ = idx + m * sy
+    kappa = -S[idx, j] - S[idx, l_] + S[j, l_]
+    assert np.all(kappa > 0)
+    inside_slots = np.zeros(n)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if (dx, dy, dz) != (0, 0, 0):
+                    inside_slots += ((x + dx >= 0) & (x + dx < m) & (y + dy >= 0) & (y + dy < m)
+                                     & (z + dz >= 0) & (z + dz < m))
+    surplus = np.diag(S) - (np.abs(S).sum(axis=1) - np.abs(np.diag(S)))
+    np.testing.assert_allclose(surplus, (26 - inside_slots) * kappa, rtol=1e-10, atol=1e-12 * np.abs(S).max())
+    # and the recovered k reproduces every coupling
+    rows, cols = np.nonzero(S)
+    offd = rows != cols
+    np.testing.assert_allclose(S[rows[offd], cols[offd]], -(kappa[rows[offd]] + kappa[cols[offd]]) / 2, rtol=1e-12)
