@@ -184,3 +184,44 @@ def test_hetero27_dirichlet_surplus():
     rows, cols = np.nonzero(S)
     offd = rows != cols
     np.testing.assert_allclose(S[rows[offd], cols[offd]], -(kappa[rows[offd]] + kappa[cols[offd]]) / 2, rtol=1e-12)
+
+
+def test_batch_problems_contract():
+    """Each system of the uneven batch is a 7- or 27-point stencil on an m^3
+    grid with nmin <= m <= nmax, symmetric, with b = A x*; both stencils occur
+    and the draws are reproducible."""
+    items = W.batch_problems(16, seed0=1000, nmin=3, nmax=7)
+    kinds = set()
+    for A, b, xs in items:
+        m = round(A.n ** (1 / 3))
+        assert m ** 3 == A.n and 3 <= m <= 7
+        if A.nnz == 7 * m ** 3 - 6 * m ** 2:
+            kinds.add(7)
+        else:
+            assert A.nnz == (3 * m - 2) ** 3
+            kinds.add(27)
+        assert _sym_ok(A)
+        np.testing.assert_allclose(A.to_scipy() @ xs, b, rtol=1e-12, atol=1e-12)
+        assert np.all(np.abs(xs) <= 1)
+    assert kinds == {7, 27}
+    again = W.batch_problems(16, seed0=1000, nmin=3, nmax=7)
+    assert all(np.array_equal(a[1], c[1]) for a, c in zip(items, again))
+
+
+def test_learned_family_contract():
+    """The learned-shift family mixes curl-curl (3 m (m+1)^2 edges), 3-DOF
+    vector Laplacian (3 m^3) and 27-point (m^3, (3m - 2)^3 nonzeros) systems,
+    each symmetric, in a random input order."""
+    fam = W.learned_family(24, 5000, cc_m=(2, 3), vl_m=(2, 3), st_m=(3, 4))
+    kinds = set()
+    for A, b in fam:
+        assert _sym_ok(A) and len(b) == A.n
+        if A.n in (3 * 2 * 9, 3 * 3 * 16):
+            kinds.add("curl")
+        elif A.n in (3 * 8, 3 * 27):
+            kinds.add("veclap")
+        else:
+            m = round(A.n ** (1 / 3))
+            assert m ** 3 == A.n and A.nnz == (3 * m - 2) ** 3
+            kinds.add("stencil27")
+    assert kinds == {"curl", "veclap", "stencil27"}
