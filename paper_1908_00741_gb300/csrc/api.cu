@@ -25,7 +25,7 @@ struct hbmc_ctx {
   HostLayout h;
   DeviceLayout d;
   hbmc_options opt{};
-  std::string err;
+  mutable std::string err;  // set by the getters that take a const context too
   int device = 0;
   bool host_only = false;
   bool factored = false;
@@ -60,7 +60,7 @@ struct DeviceGuard {
   }
 };
 
-hbmc_status set_err(hbmc_ctx *c, hbmc_status s, const std::string &msg) {
+hbmc_status set_err(const hbmc_ctx *c, hbmc_status s, const std::string &msg) {
   if (c) c->err = msg; else g_err = msg;
   return s;
 }
@@ -596,7 +596,7 @@ hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info) {
 hbmc_status hbmc_get_split(const hbmc_ctx *ctx, int32_t *head) {
   if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
   const HostLayout &h = ctx->h;
-  if (h.split_piece <= 0) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "the context was built without row splitting");
+  if (h.split_piece <= 0) return set_err(ctx, HBMC_ERR_INVALID_ARG, "the context was built without row splitting");
   if (head && !h.split_head.empty()) std::memcpy(head, h.split_head.data(), sizeof(int32_t) * h.split_head.size());
   return HBMC_OK;
 }
@@ -604,7 +604,7 @@ hbmc_status hbmc_get_split(const hbmc_ctx *ctx, int32_t *head) {
 hbmc_status hbmc_get_vslice(const hbmc_ctx *ctx, int32_t *height) {
   if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
   const HostLayout &h = ctx->h;
-  if (h.vslice_cost <= 0) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "the context was built without sell_vslice");
+  if (h.vslice_cost <= 0) return set_err(ctx, HBMC_ERR_INVALID_ARG, "the context was built without sell_vslice");
   if (height)
     for (size_t s = 0; s < h.vs_c.size(); ++s) height[s] = h.vs_c[s];
   return HBMC_OK;
@@ -613,20 +613,20 @@ hbmc_status hbmc_get_vslice(const hbmc_ctx *ctx, int32_t *height) {
 hbmc_status hbmc_get_dag_deps(const hbmc_ctx *ctx, int32_t dir, int64_t *ptr, int32_t *dep, int64_t cap,
                               int64_t *count) {
   if (!ctx) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "null context");
-  if (dir != 0 && dir != 1) return set_err(nullptr, HBMC_ERR_INVALID_ARG, "dir must be 0 (forward) or 1 (backward)");
+  if (dir != 0 && dir != 1) return set_err(ctx, HBMC_ERR_INVALID_ARG, "dir must be 0 (forward) or 1 (backward)");
   hbmc::DagTables t;
   try {
     if (!hbmc::dag_host_tables(ctx->h, t))
-      return set_err(nullptr, HBMC_ERR_INVALID_ARG,
+      return set_err(ctx, HBMC_ERR_INVALID_ARG,
                      "the dependency-driven sweeps need w = 32 and at least one level-1 block");
   } catch (const std::bad_alloc &) {
-    return set_err(nullptr, HBMC_ERR_OOM, "host allocation failed");
+    return set_err(ctx, HBMC_ERR_OOM, "host allocation failed");
   }
   const std::vector<int64_t> &p = dir == 0 ? t.ptr_f : t.ptr_b;
   const std::vector<int32_t> &v = dir == 0 ? t.dep_f : t.dep_b;
   if (count) *count = (int64_t)v.size();
   if (dep && cap < (int64_t)v.size())
-    return set_err(nullptr, HBMC_ERR_INVALID_ARG, "cap is smaller than the number of entries");
+    return set_err(ctx, HBMC_ERR_INVALID_ARG, "cap is smaller than the number of entries");
   if (ptr) std::memcpy(ptr, p.data(), sizeof(int64_t) * p.size());
   if (dep && !v.empty()) std::memcpy(dep, v.data(), sizeof(int32_t) * v.size());
   return HBMC_OK;

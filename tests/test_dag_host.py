@@ -152,7 +152,7 @@ def test_dag_deps_arguments(lib):
     ctx = H.hbmc_build(A, 8, 32, box=(2, 2, 2), host_only=True)
     try:
         for bad in (-1, 2):
-            with pytest.raises(H.HbmcError):
+            with pytest.raises(H.HbmcError, match="dir must be 0"):
                 H.hbmc_get_dag_deps(ctx, bad)
         import ctypes
         count = ctypes.c_int64(-1)
@@ -167,7 +167,7 @@ def test_dag_deps_arguments(lib):
         ctx.close()
     ctx = H.hbmc_build(A, 8, 16, box=(2, 2, 2), host_only=True)
     try:
-        with pytest.raises(H.HbmcError):
+        with pytest.raises(H.HbmcError, match="need w = 32"):
             H.hbmc_get_dag_deps(ctx, 0)
     finally:
         ctx.close()

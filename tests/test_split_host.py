@@ -46,7 +46,7 @@ def test_host_split_argument_checks(lib):
         H.hbmc_build(A, 8, 32, host_only=True, sell_split=4, sell_split_cost=-2)
     ctx = H.hbmc_build(A, 8, 32, host_only=True)
     assert ctx.info()["sell_entries_split"] == 0
-    with pytest.raises(H.HbmcError):
+    with pytest.raises(H.HbmcError, match="without row splitting"):
         H.hbmc_get_split(ctx)
 
 
