@@ -205,6 +205,8 @@ const char *hbmc_last_error(const hbmc_ctx *ctx);
 /* Static name of a status code. */
 const char *hbmc_status_string(hbmc_status s);
 
+/* Fills *info (the fields of hbmc_info_t above) from ctx; works for host_only
+ * contexts.  INVALID_ARG when ctx or info is NULL. */
 hbmc_status hbmc_info(const hbmc_ctx *ctx, hbmc_info_t *info);
 
 /*
